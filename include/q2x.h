@@ -1,0 +1,171 @@
+/*
+ * q2x.h -- C ABI of the Q2X (quadrature-to-expansion) library for GB300.
+ *
+ * Q2X computes, for every simplex element (line segment, flat triangle,
+ * tetrahedron) carrying a density, the multipole coefficients of its Laplace
+ * layer potential about an expansion centre r*, up to degree p, and sums them
+ * into one coefficient vector per octree leaf box (Sec. 2, Eq. (st4)):
+ *
+ *   K_n^m = J/(4pi) (-1)^n p_n^{-m}   segment,     single layer   Eq. (bas10)
+ *   L_n^m = J/(4pi) (-1)^n i_n^{-m}   triangle,    single layer
+ *   M_n^m = J/(4pi) (-1)^n l_n^{-m}   triangle,    double layer
+ *   N_n^m = J/(4pi) (-1)^n a_n^{-m}   tetrahedron, single (volume) layer
+ *
+ * with R_n^m normalised as in Eq. (bas1), J the Jacobian of Eq. (map4) and
+ * p_n^m, i_n^m, a_n^m the integrals of Eq. (bas9) of R_n^m(y - r*) over the
+ * unit simplices.  They are computed by the paper's O(1)-per-moment recursions
+ * (Lemmas 1-5, Eqs. (rec10)-(rec15)) in CUDA kernels for sm_103a.
+ *
+ * CONVENTIONS (all entry points)
+ *  - Degree: p is the MAXIMUM degree kept, n = 0..p, so (p+1)^2 real numbers
+ *    per expansion.  (The paper's truncation number counts degrees 0..p-1.)
+ *  - Packing: real index k = n*n + n + m, -n <= m <= n.  Entry k holds
+ *    Re F_n^m for m >= 0 and Im F_n^{|m|} for m < 0 (negative orders follow
+ *    from F_n^{-m} = (-1)^m conj(F_n^m), Eq. (bas2.1); Im F_n^0 = 0).
+ *  - Norm: Q2X_NORM_COEFF gives the coefficients above (expansion of the
+ *    potential in S_n^m, Eq. (bas3)); Q2X_NORM_MOMENT gives the raw moments
+ *    int density * R_n^m(y - r*) (double layer: int density * n.grad R_n^m).
+ *  - Memory: every array pointer is DEVICE memory owned by the caller.  The
+ *    plan owns its workspace.  SoA layouts:
+ *      vxyz   double[3 * n_vert]    x block, then y block, then z block
+ *      idx    int32 [k * n_elem]    vertex j of element e at idx[j*n_elem + e]
+ *                                   (k = 2 segment, 3 triangle, 4 tetrahedron;
+ *                                    vertex order x1, x2, x3[, x4] of Eq. (map2))
+ *      leaf_off int64[n_leaves + 1] CSR: elements of leaf L are
+ *                                   [leaf_off[L], leaf_off[L+1]); elements must
+ *                                   be sorted by leaf; leaf_off[0] = 0,
+ *                                   leaf_off[n_leaves] = n_elem
+ *      leaf_c double[3 * n_leaves]  expansion centres r* (SoA)
+ *      leaf_rho double[n_leaves]    length scale of each leaf (e.g. its
+ *                                   half-diagonal or the largest distance from
+ *                                   r* to a vertex); only the power of two
+ *                                   above it is used, to keep the FP32 path in
+ *                                   range.  NULL: computed from the geometry
+ *      leaf_p int32[n_leaves]       per-leaf degree 0..p_max, NULL = p_max;
+ *                                   entries above a leaf's degree are zero
+ *      coef   double[n_leaves * (p_max+1)^2]   output, real packing
+ *    leaf_off == NULL selects per-element expansions: n_leaves must equal
+ *    n_elem and leaf_c holds one centre per element.
+ *  - accumulate: 0 overwrites coef, 1 adds into it (several element kinds
+ *    into the same leaves).
+ *  - Streams: calls are asynchronous on the plan's stream.  Host-side argument
+ *    checks return a status synchronously.  Device-side checks (vertex index
+ *    out of range, non-finite input, bad leaf degree, bad leaf offsets) set a
+ *    device error word; q2x_sync() (or the next call on the plan) reports it as
+ *    Q2X_ERR_DEVICE_INPUT and clears it.  Invalid elements contribute zero.
+ *  - No CPU fallback: without a usable CUDA device every call fails with
+ *    Q2X_ERR_CUDA.  No exception crosses the ABI.
+ *  - Thread safety: a plan may be used by one host thread at a time; distinct
+ *    plans are independent.
+ */
+#ifndef Q2X_H
+#define Q2X_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    Q2X_OK = 0,
+    Q2X_ERR_ARG = 1,          /* bad argument (NULL pointer, negative size, ...) */
+    Q2X_ERR_RANGE = 2,        /* p outside 0..Q2X_P_MAX or above the plan's p_max */
+    Q2X_ERR_CUDA = 3,         /* a CUDA runtime call failed (message in q2x_last_error) */
+    Q2X_ERR_OOM = 4,          /* workspace allocation failed */
+    Q2X_ERR_DEVICE_INPUT = 5, /* the device error word was set by a previous call */
+    Q2X_ERR_TIMEOUT = 6,      /* reserved: a bounded device wait gave up */
+    Q2X_ERR_UNSUPPORTED = 7   /* combination not implemented */
+} q2x_status;
+
+typedef enum { Q2X_NORM_COEFF = 0, Q2X_NORM_MOMENT = 1 } q2x_norm;
+typedef enum { Q2X_FP64 = 0, Q2X_FP32_MIXED = 1 } q2x_precision;
+typedef enum { Q2X_DENSITY_CONST = 0, Q2X_DENSITY_LINEAR = 1 } q2x_density;
+
+#define Q2X_P_MAX 20
+
+/* Bits of the device error word (q2x_device_errors). */
+#define Q2X_DEVERR_INDEX 1u      /* a vertex index outside [0, n_vert) */
+#define Q2X_DEVERR_NONFINITE 2u  /* a non-finite coordinate, centre or density */
+#define Q2X_DEVERR_LEAF_P 4u     /* leaf_p outside [0, p_max] */
+#define Q2X_DEVERR_LEAF_OFF 8u   /* leaf_off not monotone or not spanning [0, n_elem] */
+
+typedef struct q2x_plan_s* q2x_plan_t;
+
+/* Create a plan for degrees up to p_max (0..Q2X_P_MAX) in the given norm and
+ * precision, bound to a CUDA stream (cudaStream_t; NULL = legacy default
+ * stream) on the current device.  Q2X_FP64 runs the whole recursion in FP64.
+ * Q2X_FP32_MIXED runs it in FP32 in a per-leaf scaled local frame; the
+ * translation to the leaf centre keeps FP64 accuracy (exact double -> float
+ * splitting), per-leaf sums are FP32 with compensated combination of partial
+ * sums, and the result is rescaled exactly into FP64.
+ * Ownership: *out must be released with q2x_plan_destroy. */
+q2x_status q2x_plan(q2x_plan_t* out, int p_max, q2x_norm norm, q2x_precision precision,
+                    void* cuda_stream);
+q2x_status q2x_plan_destroy(q2x_plan_t plan);
+q2x_status q2x_plan_set_stream(q2x_plan_t plan, void* cuda_stream);
+
+/* Last error message of this plan (static storage owned by the plan), or of
+ * the last failed q2x_plan() call when plan == NULL. */
+const char* q2x_last_error(q2x_plan_t plan);
+
+/* Synchronise the plan's stream; return Q2X_ERR_DEVICE_INPUT (and clear the
+ * word) if any device-side check failed since the last report. */
+q2x_status q2x_sync(q2x_plan_t plan);
+/* Synchronise and return the raw device error bits (Q2X_DEVERR_*), clearing them. */
+q2x_status q2x_device_errors(q2x_plan_t plan, uint32_t* bits);
+
+/* Pre-size the workspace for up to n_elem elements and n_leaves leaves so that
+ * later calls of that size allocate nothing (needed before graph capture). */
+q2x_status q2x_reserve(q2x_plan_t plan, int64_t n_elem, int64_t n_leaves);
+/* Bytes of device workspace the plan currently holds. */
+int64_t q2x_workspace_bytes(q2x_plan_t plan);
+
+/* Segments: K coefficients (Lemma 1, Eqs. (rec10)-(rec11)), constant line
+ * density sigma[n_elem]; Jacobian |x2 - x1|. */
+q2x_status q2x_segments(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const double* vxyz,
+                        const int32_t* idx, const double* sigma, int64_t n_leaves,
+                        const int64_t* leaf_off, const double* leaf_c, const double* leaf_rho,
+                        const int32_t* leaf_p, double* coef, int accumulate);
+
+/* Triangles, single and/or double layer in ONE pass (Lemmas 2-3,
+ * Eqs. (rec12)-(rec15)).  density Q2X_DENSITY_CONST: sigma[n_elem];
+ * Q2X_DENSITY_LINEAR: sigma[n_vert] (value at each vertex, interpolated
+ * linearly over the triangle).  coef_single (L) and/or coef_double (M) may be
+ * NULL to skip that layer (not both).  The double-layer normal is
+ * n = (x2 - x1) x (x3 - x1) / J (right-hand rule on the vertex order). */
+q2x_status q2x_triangles(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const double* vxyz,
+                         const int32_t* idx, q2x_density density, const double* sigma,
+                         int64_t n_leaves, const int64_t* leaf_off, const double* leaf_c,
+                         const double* leaf_rho, const int32_t* leaf_p, double* coef_single,
+                         double* coef_double, int accumulate);
+q2x_status q2x_triangles_single(q2x_plan_t plan, int64_t n_elem, int64_t n_vert,
+                                const double* vxyz, const int32_t* idx, q2x_density density,
+                                const double* sigma, int64_t n_leaves, const int64_t* leaf_off,
+                                const double* leaf_c, const double* leaf_rho,
+                                const int32_t* leaf_p, double* coef, int accumulate);
+q2x_status q2x_triangles_double(q2x_plan_t plan, int64_t n_elem, int64_t n_vert,
+                                const double* vxyz, const int32_t* idx, q2x_density density,
+                                const double* sigma, int64_t n_leaves, const int64_t* leaf_off,
+                                const double* leaf_c, const double* leaf_rho,
+                                const int32_t* leaf_p, double* coef, int accumulate);
+
+/* Tetrahedra: N coefficients (Lemmas 4-5, Eqs. (rec14.1)-(rec14.2)),
+ * constant volume density sigma[n_elem]; Jacobian |(Ru x Rv).Rw|. */
+q2x_status q2x_tetra(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const double* vxyz,
+                     const int32_t* idx, const double* sigma, int64_t n_leaves,
+                     const int64_t* leaf_off, const double* leaf_c, const double* leaf_rho,
+                     const int32_t* leaf_p, double* coef, int accumulate);
+
+/* Segmented sum of per-element coefficient rows into leaves (Eq. (st4)):
+ * coef[L] (+)= sum_{e in leaf L} elem[e], elem double[n_elem * (p+1)^2],
+ * coef double[n_leaves * (p+1)^2], leaf_off as above (required).  FP64,
+ * deterministic (fixed summation order).  p <= the plan's p_max. */
+q2x_status q2x_leaf_reduce(q2x_plan_t plan, int64_t n_elem, int p, const double* elem,
+                           int64_t n_leaves, const int64_t* leaf_off, double* coef,
+                           int accumulate);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* Q2X_H */

@@ -1,0 +1,508 @@
+// q2x_api.cu -- C ABI of the Q2X library (declared in include/q2x.h):
+// argument checks, plan and workspace management, kernel dispatch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "q2x.h"
+#include "q2x_kernels.cuh"
+
+// explicit instantiations live in q2x_inst_*.cu
+Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_SEG, q2x::DENS_CONST)
+Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_TRI, q2x::DENS_CONST)
+Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_TRI, q2x::DENS_LINEAR)
+Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_TET, q2x::DENS_CONST)
+Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_SEG, q2x::DENS_CONST)
+Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_TRI, q2x::DENS_CONST)
+Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_TRI, q2x::DENS_LINEAR)
+Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_TET, q2x::DENS_CONST)
+
+namespace {
+
+struct KernelEntry {
+    cudaError_t (*launch)(const q2x::ElemArgs&, int, size_t, cudaStream_t);
+    cudaError_t (*occupancy)(int*, size_t);
+};
+
+constexpr int kNumBins = 5;
+constexpr int kBins[kNumBins] = {4, 8, 12, 16, 20};
+
+#define Q2X_ENTRY(T, P, KIND, DENS) {&q2x::launch_elem<T, P, KIND, DENS>, &q2x::occupancy_elem<T, P, KIND, DENS>},
+#define Q2X_ROW(T, KIND, DENS) {Q2X_FOR_BINS(Q2X_ENTRY, T, KIND, DENS)},
+// [precision: 0 FP64, 1 FP32][combo: seg, tri const, tri linear, tet][bin]
+const KernelEntry kTable[2][4][kNumBins] = {
+    {Q2X_ROW(double, q2x::KIND_SEG, q2x::DENS_CONST) Q2X_ROW(double, q2x::KIND_TRI, q2x::DENS_CONST)
+         Q2X_ROW(double, q2x::KIND_TRI, q2x::DENS_LINEAR) Q2X_ROW(double, q2x::KIND_TET, q2x::DENS_CONST)},
+    {Q2X_ROW(float, q2x::KIND_SEG, q2x::DENS_CONST) Q2X_ROW(float, q2x::KIND_TRI, q2x::DENS_CONST)
+         Q2X_ROW(float, q2x::KIND_TRI, q2x::DENS_LINEAR) Q2X_ROW(float, q2x::KIND_TET, q2x::DENS_CONST)},
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct q2x_plan_s {
+    int p_max = 0;
+    int norm = 0;
+    int prec = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    unsigned* d_err = nullptr;
+    unsigned* h_err = nullptr;  // pinned
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int occ_cache[2][4][kNumBins] = {};
+    std::string last_error;
+};
+
+namespace {
+
+q2x_status fail(q2x_plan_t plan, q2x_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (plan)
+        plan->last_error = buf;
+    else
+        g_create_error = buf;
+    return st;
+}
+
+q2x_status cuda_fail(q2x_plan_t plan, cudaError_t e, const char* what)
+{
+    return fail(plan, Q2X_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// grow the workspace to at least `bytes` (synchronises the plan's stream
+// before releasing the old buffer)
+q2x_status ensure_ws(q2x_plan_t plan, size_t bytes)
+{
+    if (bytes <= plan->ws_bytes) return Q2X_OK;
+    cudaError_t e;
+    if (plan->ws) {
+        e = cudaStreamSynchronize(plan->stream);
+        if (e != cudaSuccess) return cuda_fail(plan, e, "cudaStreamSynchronize");
+        cudaFree(plan->ws);
+        plan->ws = nullptr;
+        plan->ws_bytes = 0;
+    }
+    bytes = align_up(std::max<size_t>(bytes, 1 << 20), 1 << 20);
+    e = cudaMalloc(&plan->ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(plan, Q2X_ERR_OOM, "workspace allocation of %zu bytes failed", bytes);
+    }
+    plan->ws_bytes = bytes;
+    return Q2X_OK;
+}
+
+int bin_index(int p)
+{
+    for (int b = 0; b < kNumBins; ++b)
+        if (p <= kBins[b]) return b;
+    return -1;
+}
+
+// ------------------------------------------------------------ small kernels
+
+// leaf_off must be non-decreasing with leaf_off[0] = 0, leaf_off[n_leaves] = n_elem
+__global__ void check_leaf_off_kernel(const int64_t* off, int64_t n_leaves, int64_t n_elem,
+                                      unsigned* err)
+{
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L > n_leaves) return;
+    const int64_t o = off[L];
+    bool bad = (o < 0 || o > n_elem);
+    if (L == 0 && o != 0) bad = true;
+    if (L == n_leaves && o != n_elem) bad = true;
+    if (L < n_leaves && off[L + 1] < o) bad = true;
+    if (bad) atomicOr(err, Q2X_DEVERR_LEAF_OFF);
+}
+
+// per-leaf scale: largest distance from the centre to a vertex of its
+// elements, as the bit pattern of a non-negative float (atomicMax on ints
+// orders non-negative floats correctly)
+__global__ void leaf_rho_kernel(int64_t n_elem, int64_t n_vert, int nv, const double* vx,
+                                const double* vy, const double* vz, const int32_t* idx,
+                                int64_t n_leaves, const int64_t* off, const double* leaf_c,
+                                int* rho_bits)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_elem) return;
+    int64_t L = e;
+    if (off) L = q2x::leaf_search(off, 0, n_leaves - 1, e);
+    const double cx = leaf_c[L], cy = leaf_c[n_leaves + L], cz = leaf_c[2 * n_leaves + L];
+    float dmax = 0.f;
+    for (int k = 0; k < nv; ++k) {
+        int64_t v = idx[(int64_t)k * n_elem + e];
+        if (v < 0 || v >= n_vert) continue;
+        const float dx = (float)(vx[v] - cx), dy = (float)(vy[v] - cy), dz = (float)(vz[v] - cz);
+        const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+        if (d == d) dmax = fmaxf(dmax, d);
+    }
+    atomicMax(rho_bits + L, __float_as_int(dmax));
+}
+
+__global__ void rho_bits_to_double(const int* bits, double* rho, int64_t n)
+{
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L < n) rho[L] = (double)__int_as_float(bits[L]);
+}
+
+// segmented sum of per-element rows: one warp per leaf, lanes over columns,
+// elements in index order (deterministic)
+__global__ void leaf_reduce_kernel(const double* __restrict__ elem, int np, int64_t n_elem,
+                                   int64_t n_leaves, const int64_t* __restrict__ off, double* coef,
+                                   int accumulate)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t L = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (L >= n_leaves) return;
+    // clamped: a bad leaf_off is reported by check_leaf_off_kernel, never read past
+    const int64_t e0 = min(max(off[L], (int64_t)0), n_elem);
+    const int64_t e1 = min(max(off[L + 1], e0), n_elem);
+    for (int c0 = 0; c0 < np; c0 += 32 * 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t e = e0; e < e1; ++e) {
+            const double* row = elem + e * np;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = c0 + k * 32 + lane;
+                if (c < np) acc[k] += __ldg(row + c);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c0 + k * 32 + lane;
+            if (c < np) {
+                double* d = coef + L * np + c;
+                *d = accumulate ? *d + acc[k] : acc[k];
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------- dispatch
+
+q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int64_t n_vert,
+                        const double* vxyz, const int32_t* idx, const double* sigma,
+                        int64_t n_leaves, const int64_t* leaf_off, const double* leaf_c,
+                        const double* leaf_rho, const int32_t* leaf_p, double* coef0,
+                        double* coef1, int accumulate)
+{
+    if (!plan) return fail(nullptr, Q2X_ERR_ARG, "plan is NULL");
+    if (n_elem < 0 || n_vert < 0 || n_leaves < 0)
+        return fail(plan, Q2X_ERR_ARG, "negative size (n_elem=%lld n_vert=%lld n_leaves=%lld)",
+                    (long long)n_elem, (long long)n_vert, (long long)n_leaves);
+    if (!coef0 && !coef1) return fail(plan, Q2X_ERR_ARG, "no output requested");
+    if (accumulate != 0 && accumulate != 1) return fail(plan, Q2X_ERR_ARG, "accumulate must be 0 or 1");
+    if (!leaf_off && n_leaves != n_elem)
+        return fail(plan, Q2X_ERR_ARG, "per-element mode (leaf_off NULL) needs n_leaves == n_elem");
+    if (n_elem > 0) {
+        if (!vxyz || !idx || !sigma) return fail(plan, Q2X_ERR_ARG, "vxyz, idx and sigma must be non-NULL");
+        if (n_vert <= 0) return fail(plan, Q2X_ERR_ARG, "n_vert must be positive");
+        if (n_leaves <= 0) return fail(plan, Q2X_ERR_ARG, "n_leaves must be positive");
+        if (n_elem > ((int64_t)1 << 40)) return fail(plan, Q2X_ERR_ARG, "n_elem too large");
+    }
+    if (n_leaves > 0 && !leaf_c) return fail(plan, Q2X_ERR_ARG, "leaf_c must be non-NULL");
+    if (dens != Q2X_DENSITY_CONST && dens != Q2X_DENSITY_LINEAR)
+        return fail(plan, Q2X_ERR_ARG, "bad density mode %d", dens);
+
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "cudaSetDevice");
+    const int np = (plan->p_max + 1) * (plan->p_max + 1);
+
+    if (n_elem == 0) {
+        if (!accumulate && n_leaves > 0) {
+            for (double* c : {coef0, coef1})
+                if (c) {
+                    e = cudaMemsetAsync(c, 0, sizeof(double) * (size_t)n_leaves * np, plan->stream);
+                    if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMemsetAsync");
+                }
+        }
+        return Q2X_OK;
+    }
+
+    const int prec = plan->prec;  // 0 FP64, 1 FP32-mixed
+    const int combo = (kind == q2x::KIND_SEG) ? 0 : (kind == q2x::KIND_TET) ? 3 : (dens == Q2X_DENSITY_LINEAR ? 2 : 1);
+    const int nv = kind + 2;
+    const int bin = bin_index(plan->p_max);
+    if (bin < 0) return fail(plan, Q2X_ERR_RANGE, "p_max %d above %d", plan->p_max, Q2X_P_MAX);
+    const KernelEntry& ke = kTable[prec][combo][bin];
+    const size_t elt = prec ? sizeof(float) : sizeof(double);
+    const size_t smem = q2x::WARPS_PER_CTA *
+                        (prec ? q2x::warp_smem_bytes<float>(np) : q2x::warp_smem_bytes<double>(np));
+
+    int& occ = plan->occ_cache[prec][combo][bin];
+    if (occ == 0) {
+        e = ke.occupancy(&occ, smem);
+        if (e != cudaSuccess) return cuda_fail(plan, e, "occupancy query");
+        if (occ <= 0) return fail(plan, Q2X_ERR_CUDA, "kernel does not fit on the device (smem %zu)", smem);
+    }
+    const int64_t resident_warps = (int64_t)occ * q2x::WARPS_PER_CTA * plan->num_sms;
+    int64_t T = (n_elem + resident_warps - 1) / resident_warps;
+    T = std::max<int64_t>(32, (T + 31) / 32 * 32);
+    const int64_t n_ranges = (n_elem + T - 1) / T;
+
+    // workspace: slots, then per-leaf scale (FP32 without leaf_rho)
+    const bool need_rho = prec == 1 && leaf_rho == nullptr;
+    const size_t slot_bytes = align_up(elt * (size_t)n_ranges * 2 * 2 * np, 256);
+    const size_t rho_bytes = need_rho ? align_up(sizeof(double) * (size_t)n_leaves, 256) : 0;
+    const size_t bits_bytes = need_rho ? align_up(sizeof(int) * (size_t)n_leaves, 256) : 0;
+    q2x_status st = ensure_ws(plan, slot_bytes + rho_bytes + bits_bytes);
+    if (st != Q2X_OK) return st;
+    unsigned char* ws = static_cast<unsigned char*>(plan->ws);
+
+    if (leaf_off) {
+        const int64_t nb = (n_leaves + 1 + 255) / 256;
+        check_leaf_off_kernel<<<(unsigned)nb, 256, 0, plan->stream>>>(leaf_off, n_leaves, n_elem, plan->d_err);
+    }
+    if (need_rho) {
+        int* bits = reinterpret_cast<int*>(ws + slot_bytes + rho_bytes);
+        double* rho = reinterpret_cast<double*>(ws + slot_bytes);
+        e = cudaMemsetAsync(bits, 0, sizeof(int) * (size_t)n_leaves, plan->stream);
+        if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMemsetAsync");
+        leaf_rho_kernel<<<(unsigned)((n_elem + 255) / 256), 256, 0, plan->stream>>>(
+            n_elem, n_vert, nv, vxyz, vxyz + n_vert, vxyz + 2 * n_vert, idx, n_leaves, leaf_off, leaf_c, bits);
+        rho_bits_to_double<<<(unsigned)((n_leaves + 255) / 256), 256, 0, plan->stream>>>(bits, rho, n_leaves);
+        leaf_rho = rho;
+    }
+
+    q2x::ElemArgs a;
+    a.n_elem = n_elem;
+    a.n_vert = n_vert;
+    a.vx = vxyz;
+    a.vy = vxyz + n_vert;
+    a.vz = vxyz + 2 * n_vert;
+    a.idx = idx;
+    a.sigma = sigma;
+    a.n_leaves = n_leaves;
+    a.leaf_off = leaf_off;
+    a.leaf_c = leaf_c;
+    a.leaf_rho = leaf_rho;
+    a.leaf_p = leaf_p;
+    a.p_max = plan->p_max;
+    a.np_max = np;
+    a.coef[0] = coef0;
+    a.coef[1] = (kind == q2x::KIND_TRI) ? coef1 : nullptr;
+    a.accumulate = accumulate;
+    a.norm = plan->norm;
+    a.T = T;
+    a.n_ranges = n_ranges;
+    a.slots = ws;
+    a.err = plan->d_err;
+
+    const int grid = (int)((n_ranges + q2x::WARPS_PER_CTA - 1) / q2x::WARPS_PER_CTA);
+    e = ke.launch(a, grid, smem, plan->stream);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "element kernel launch");
+    if (leaf_off && n_ranges > 1) {
+        const int d_out = (kind == q2x::KIND_SEG) ? 1 : (kind == q2x::KIND_TET) ? 3 : (dens == Q2X_DENSITY_LINEAR ? 3 : 2);
+        const int64_t nw = n_ranges - 1;
+        const int fgrid = (int)((nw + 3) / 4);
+        if (prec)
+            q2x::q2x_fixup_kernel<float><<<fgrid, 128, 0, plan->stream>>>(a, kind + 1, d_out, d_out - 1);
+        else
+            q2x::q2x_fixup_kernel<double><<<fgrid, 128, 0, plan->stream>>>(a, kind + 1, d_out, d_out - 1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(plan, e, "fixup kernel launch");
+    }
+    return Q2X_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+q2x_status q2x_plan(q2x_plan_t* out, int p_max, q2x_norm norm, q2x_precision precision,
+                    void* cuda_stream)
+{
+    if (!out) return fail(nullptr, Q2X_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (p_max < 0 || p_max > Q2X_P_MAX)
+        return fail(nullptr, Q2X_ERR_RANGE, "p_max %d outside 0..%d", p_max, Q2X_P_MAX);
+    if (norm != Q2X_NORM_COEFF && norm != Q2X_NORM_MOMENT) return fail(nullptr, Q2X_ERR_ARG, "bad norm %d", (int)norm);
+    if (precision != Q2X_FP64 && precision != Q2X_FP32_MIXED)
+        return fail(nullptr, Q2X_ERR_ARG, "bad precision %d", (int)precision);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, Q2X_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(nullptr, Q2X_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
+    q2x_plan_s* p = new q2x_plan_s();
+    p->p_max = p_max;
+    p->norm = (int)norm;
+    p->prec = (precision == Q2X_FP32_MIXED) ? 1 : 0;
+    p->stream = static_cast<cudaStream_t>(cuda_stream);
+    p->device = dev;
+    p->num_sms = sms;
+    e = cudaMalloc(&p->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMallocHost(&p->h_err, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (p->d_err) cudaFree(p->d_err);
+        delete p;
+        return fail(nullptr, Q2X_ERR_CUDA, "plan allocation: %s", cudaGetErrorString(e));
+    }
+    *out = p;
+    return Q2X_OK;
+}
+
+q2x_status q2x_plan_destroy(q2x_plan_t plan)
+{
+    if (!plan) return Q2X_ERR_ARG;
+    cudaSetDevice(plan->device);
+    cudaStreamSynchronize(plan->stream);
+    if (plan->ws) cudaFree(plan->ws);
+    if (plan->d_err) cudaFree(plan->d_err);
+    if (plan->h_err) cudaFreeHost(plan->h_err);
+    delete plan;
+    return Q2X_OK;
+}
+
+q2x_status q2x_plan_set_stream(q2x_plan_t plan, void* cuda_stream)
+{
+    if (!plan) return Q2X_ERR_ARG;
+    plan->stream = static_cast<cudaStream_t>(cuda_stream);
+    return Q2X_OK;
+}
+
+const char* q2x_last_error(q2x_plan_t plan) { return plan ? plan->last_error.c_str() : g_create_error.c_str(); }
+
+q2x_status q2x_device_errors(q2x_plan_t plan, uint32_t* bits)
+{
+    if (!plan || !bits) return Q2X_ERR_ARG;
+    cudaSetDevice(plan->device);
+    cudaError_t e = cudaMemcpyAsync(plan->h_err, plan->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, plan->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "reading the device error word");
+    *bits = *plan->h_err;
+    if (*bits) {
+        e = cudaMemsetAsync(plan->d_err, 0, sizeof(unsigned), plan->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
+        if (e != cudaSuccess) return cuda_fail(plan, e, "clearing the device error word");
+    }
+    return Q2X_OK;
+}
+
+q2x_status q2x_sync(q2x_plan_t plan)
+{
+    uint32_t bits = 0;
+    q2x_status st = q2x_device_errors(plan, &bits);
+    if (st != Q2X_OK) return st;
+    if (bits)
+        return fail(plan, Q2X_ERR_DEVICE_INPUT, "device-side input check failed (bits 0x%x:%s%s%s%s)", bits,
+                    (bits & Q2X_DEVERR_INDEX) ? " vertex index out of range" : "",
+                    (bits & Q2X_DEVERR_NONFINITE) ? " non-finite input" : "",
+                    (bits & Q2X_DEVERR_LEAF_P) ? " leaf_p out of range" : "",
+                    (bits & Q2X_DEVERR_LEAF_OFF) ? " bad leaf_off" : "");
+    return Q2X_OK;
+}
+
+q2x_status q2x_reserve(q2x_plan_t plan, int64_t n_elem, int64_t n_leaves)
+{
+    if (!plan || n_elem < 0 || n_leaves < 0) return fail(plan, Q2X_ERR_ARG, "bad reserve arguments");
+    cudaSetDevice(plan->device);
+    const int np = (plan->p_max + 1) * (plan->p_max + 1);
+    const size_t elt = plan->prec ? sizeof(float) : sizeof(double);
+    // worst case: one range per 32 elements
+    const int64_t n_ranges = (n_elem + 31) / 32;
+    const size_t bytes = align_up(elt * (size_t)n_ranges * 2 * 2 * np, 256) +
+                         align_up(sizeof(double) * (size_t)n_leaves, 256) +
+                         align_up(sizeof(int) * (size_t)n_leaves, 256);
+    return ensure_ws(plan, bytes);
+}
+
+int64_t q2x_workspace_bytes(q2x_plan_t plan) { return plan ? (int64_t)plan->ws_bytes : -1; }
+
+q2x_status q2x_segments(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const double* vxyz,
+                        const int32_t* idx, const double* sigma, int64_t n_leaves,
+                        const int64_t* leaf_off, const double* leaf_c, const double* leaf_rho,
+                        const int32_t* leaf_p, double* coef, int accumulate)
+{
+    if (!coef) return fail(plan, Q2X_ERR_ARG, "coef is NULL");
+    return run_elements(plan, q2x::KIND_SEG, Q2X_DENSITY_CONST, n_elem, n_vert, vxyz, idx, sigma,
+                        n_leaves, leaf_off, leaf_c, leaf_rho, leaf_p, coef, nullptr, accumulate);
+}
+
+q2x_status q2x_triangles(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const double* vxyz,
+                         const int32_t* idx, q2x_density density, const double* sigma,
+                         int64_t n_leaves, const int64_t* leaf_off, const double* leaf_c,
+                         const double* leaf_rho, const int32_t* leaf_p, double* coef_single,
+                         double* coef_double, int accumulate)
+{
+    return run_elements(plan, q2x::KIND_TRI, (int)density, n_elem, n_vert, vxyz, idx, sigma, n_leaves,
+                        leaf_off, leaf_c, leaf_rho, leaf_p, coef_single, coef_double, accumulate);
+}
+
+q2x_status q2x_triangles_single(q2x_plan_t plan, int64_t n_elem, int64_t n_vert,
+                                const double* vxyz, const int32_t* idx, q2x_density density,
+                                const double* sigma, int64_t n_leaves, const int64_t* leaf_off,
+                                const double* leaf_c, const double* leaf_rho,
+                                const int32_t* leaf_p, double* coef, int accumulate)
+{
+    if (!coef) return fail(plan, Q2X_ERR_ARG, "coef is NULL");
+    return run_elements(plan, q2x::KIND_TRI, (int)density, n_elem, n_vert, vxyz, idx, sigma, n_leaves,
+                        leaf_off, leaf_c, leaf_rho, leaf_p, coef, nullptr, accumulate);
+}
+
+q2x_status q2x_triangles_double(q2x_plan_t plan, int64_t n_elem, int64_t n_vert,
+                                const double* vxyz, const int32_t* idx, q2x_density density,
+                                const double* sigma, int64_t n_leaves, const int64_t* leaf_off,
+                                const double* leaf_c, const double* leaf_rho,
+                                const int32_t* leaf_p, double* coef, int accumulate)
+{
+    if (!coef) return fail(plan, Q2X_ERR_ARG, "coef is NULL");
+    return run_elements(plan, q2x::KIND_TRI, (int)density, n_elem, n_vert, vxyz, idx, sigma, n_leaves,
+                        leaf_off, leaf_c, leaf_rho, leaf_p, nullptr, coef, accumulate);
+}
+
+q2x_status q2x_tetra(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const double* vxyz,
+                     const int32_t* idx, const double* sigma, int64_t n_leaves,
+                     const int64_t* leaf_off, const double* leaf_c, const double* leaf_rho,
+                     const int32_t* leaf_p, double* coef, int accumulate)
+{
+    if (!coef) return fail(plan, Q2X_ERR_ARG, "coef is NULL");
+    return run_elements(plan, q2x::KIND_TET, Q2X_DENSITY_CONST, n_elem, n_vert, vxyz, idx, sigma,
+                        n_leaves, leaf_off, leaf_c, leaf_rho, leaf_p, coef, nullptr, accumulate);
+}
+
+q2x_status q2x_leaf_reduce(q2x_plan_t plan, int64_t n_elem, int p, const double* elem,
+                           int64_t n_leaves, const int64_t* leaf_off, double* coef, int accumulate)
+{
+    if (!plan) return fail(nullptr, Q2X_ERR_ARG, "plan is NULL");
+    if (p < 0 || p > plan->p_max) return fail(plan, Q2X_ERR_RANGE, "p %d outside 0..%d", p, plan->p_max);
+    if (n_elem < 0 || n_leaves < 0) return fail(plan, Q2X_ERR_ARG, "negative size");
+    if (!leaf_off || !coef || (n_elem > 0 && !elem)) return fail(plan, Q2X_ERR_ARG, "NULL pointer");
+    if (accumulate != 0 && accumulate != 1) return fail(plan, Q2X_ERR_ARG, "accumulate must be 0 or 1");
+    if (n_leaves == 0) return Q2X_OK;
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "cudaSetDevice");
+    const int np = (p + 1) * (p + 1);
+    check_leaf_off_kernel<<<(unsigned)((n_leaves + 1 + 255) / 256), 256, 0, plan->stream>>>(leaf_off, n_leaves, n_elem,
+                                                                                           plan->d_err);
+    const int warps = 8;
+    leaf_reduce_kernel<<<(unsigned)((n_leaves + warps - 1) / warps), warps * 32, 0, plan->stream>>>(
+        elem, np, n_elem, n_leaves, leaf_off, coef, accumulate);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(plan, e, "leaf_reduce launch");
+    return Q2X_OK;
+}
+
+}  // extern "C"

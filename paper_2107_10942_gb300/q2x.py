@@ -1,0 +1,189 @@
+"""Python binding of the Q2X C ABI: argument marshalling from torch CUDA
+tensors to the library's pointers and sizes.  Every computation happens in
+the CUDA library; nothing here computes a moment."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._lib import check, lib
+
+NORM_COEFF, NORM_MOMENT = 0, 1
+FP64, FP32_MIXED = 0, 1
+DENSITY_CONST, DENSITY_LINEAR = 0, 1
+_NORMS = {"coeff": 0, "moment": 1, 0: 0, 1: 1}
+_PRECS = {"fp64": 0, "fp32": 1, "fp32_mixed": 1, 0: 0, 1: 1}
+_DENS = {"const": 0, "constant": 0, "linear": 1, 0: 0, 1: 1}
+
+
+def n_coef(p: int) -> int:
+    return (p + 1) * (p + 1)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, name, shape=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if t.device.type != "cuda":
+        raise ValueError("%s must be a CUDA tensor (the library takes device pointers)" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return t
+
+
+class Plan:
+    """A q2x_plan: degree bound, normalisation, precision, stream and the
+    library-owned workspace.  Calls are asynchronous on the plan's stream;
+    `sync()` waits and raises on device-side input errors."""
+
+    def __init__(self, p_max: int, norm="coeff", precision="fp64", stream=None):
+        self.p_max = int(p_max)
+        self.norm = _NORMS[norm]
+        self.precision = _PRECS[precision]
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        h = ctypes.c_void_p()
+        # without a CUDA device the library itself reports Q2X_ERR_CUDA
+        check(lib().q2x_plan(ctypes.byref(h), self.p_max, self.norm, self.precision,
+                             ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().q2x_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._stream = stream
+        check(lib().q2x_plan_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)), self._h)
+
+    def sync(self):
+        check(lib().q2x_sync(self._h), self._h)
+
+    def device_errors(self) -> int:
+        bits = ctypes.c_uint32(0)
+        check(lib().q2x_device_errors(self._h, ctypes.byref(bits)), self._h)
+        return int(bits.value)
+
+    def reserve(self, n_elem: int, n_leaves: int):
+        check(lib().q2x_reserve(self._h, int(n_elem), int(n_leaves)), self._h)
+
+    def workspace_bytes(self) -> int:
+        return int(lib().q2x_workspace_bytes(self._h))
+
+    # ------------------------------------------------------------ helpers
+    def _leaf_args(self, n_elem, leaf_off, leaf_c, leaf_rho, leaf_p):
+        if leaf_off is None:
+            n_leaves = n_elem
+        else:
+            _need(leaf_off, torch.int64, "leaf_off")
+            n_leaves = leaf_off.shape[0] - 1
+        _need(leaf_c, torch.float64, "leaf_c", (3, n_leaves))
+        _need(leaf_rho, torch.float64, "leaf_rho", (n_leaves,))
+        _need(leaf_p, torch.int32, "leaf_p", (n_leaves,))
+        return n_leaves
+
+    def _out(self, coef, n_leaves, device, accumulate):
+        nc = n_coef(self.p_max)
+        if coef is None:
+            if accumulate:
+                raise ValueError("accumulate=True needs an output tensor")
+            return torch.empty((n_leaves, nc), dtype=torch.float64, device=device)
+        return _need(coef, torch.float64, "coef", (n_leaves, nc))
+
+    def _geom(self, vxyz, idx, nv):
+        _need(vxyz, torch.float64, "vxyz")
+        _need(idx, torch.int32, "idx")
+        if vxyz.dim() != 2 or vxyz.shape[0] != 3:
+            raise ValueError("vxyz must be (3, n_vert)")
+        if idx.dim() != 2 or idx.shape[0] != nv:
+            raise ValueError("idx must be (%d, n_elem)" % nv)
+        return vxyz.shape[1], idx.shape[1]
+
+    # ---------------------------------------------------------- elements
+    def segments(self, vxyz, idx, sigma, leaf_off, leaf_c, leaf_rho=None, leaf_p=None, coef=None,
+                 accumulate=False):
+        n_vert, n_elem = self._geom(vxyz, idx, 2)
+        _need(sigma, torch.float64, "sigma", (n_elem,))
+        n_leaves = self._leaf_args(n_elem, leaf_off, leaf_c, leaf_rho, leaf_p)
+        coef = self._out(coef, n_leaves, vxyz.device, accumulate)
+        check(lib().q2x_segments(self._h, n_elem, n_vert, _ptr(vxyz), _ptr(idx), _ptr(sigma), n_leaves,
+                                 _ptr(leaf_off), _ptr(leaf_c), _ptr(leaf_rho), _ptr(leaf_p), _ptr(coef),
+                                 int(bool(accumulate))), self._h)
+        return coef
+
+    def tetra(self, vxyz, idx, sigma, leaf_off, leaf_c, leaf_rho=None, leaf_p=None, coef=None,
+              accumulate=False):
+        n_vert, n_elem = self._geom(vxyz, idx, 4)
+        _need(sigma, torch.float64, "sigma", (n_elem,))
+        n_leaves = self._leaf_args(n_elem, leaf_off, leaf_c, leaf_rho, leaf_p)
+        coef = self._out(coef, n_leaves, vxyz.device, accumulate)
+        check(lib().q2x_tetra(self._h, n_elem, n_vert, _ptr(vxyz), _ptr(idx), _ptr(sigma), n_leaves,
+                              _ptr(leaf_off), _ptr(leaf_c), _ptr(leaf_rho), _ptr(leaf_p), _ptr(coef),
+                              int(bool(accumulate))), self._h)
+        return coef
+
+    def triangles(self, vxyz, idx, sigma, leaf_off, leaf_c, leaf_rho=None, leaf_p=None, density="const",
+                  single=True, double=False, coef_single=None, coef_double=None, accumulate=False):
+        """Single and/or double layer in one pass; returns (coef_single, coef_double)
+        with None for a layer not requested."""
+        n_vert, n_elem = self._geom(vxyz, idx, 3)
+        dens = _DENS[density]
+        _need(sigma, torch.float64, "sigma", (n_vert if dens == 1 else n_elem,))
+        n_leaves = self._leaf_args(n_elem, leaf_off, leaf_c, leaf_rho, leaf_p)
+        cs = self._out(coef_single, n_leaves, vxyz.device, accumulate) if single else None
+        cd = self._out(coef_double, n_leaves, vxyz.device, accumulate) if double else None
+        if cs is None and cd is None:
+            raise ValueError("request at least one layer")
+        check(lib().q2x_triangles(self._h, n_elem, n_vert, _ptr(vxyz), _ptr(idx), dens, _ptr(sigma), n_leaves,
+                                  _ptr(leaf_off), _ptr(leaf_c), _ptr(leaf_rho), _ptr(leaf_p), _ptr(cs), _ptr(cd),
+                                  int(bool(accumulate))), self._h)
+        return cs, cd
+
+    def leaf_reduce(self, elem, p, leaf_off, coef=None, accumulate=False):
+        _need(elem, torch.float64, "elem")
+        _need(leaf_off, torch.int64, "leaf_off")
+        nc = n_coef(p)
+        if elem.dim() != 2 or elem.shape[1] != nc:
+            raise ValueError("elem must be (n_elem, (p+1)^2)")
+        n_leaves = leaf_off.shape[0] - 1
+        if coef is None:
+            if accumulate:
+                raise ValueError("accumulate=True needs an output tensor")
+            coef = torch.empty((n_leaves, nc), dtype=torch.float64, device=elem.device)
+        _need(coef, torch.float64, "coef", (n_leaves, nc))
+        check(lib().q2x_leaf_reduce(self._h, elem.shape[0], int(p), _ptr(elem), n_leaves, _ptr(leaf_off),
+                                    _ptr(coef), int(bool(accumulate))), self._h)
+        return coef
+
+
+def problem_to_device(prob: dict, device="cuda") -> dict:
+    """Copy a workloads-style problem dict (numpy arrays) to device tensors."""
+    out = {}
+    for k, v in prob.items():
+        if hasattr(v, "dtype") and hasattr(v, "shape"):
+            out[k] = torch.from_numpy(v).to(device)
+        else:
+            out[k] = v
+    return out

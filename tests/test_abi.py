@@ -1,0 +1,54 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/q2x.h declares; without a GPU it fails loudly (no CPU fallback)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "q2x.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(q2x_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def so():
+    from paper_2107_10942_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("q2x_plan", "q2x_segments", "q2x_triangles_single", "q2x_triangles_double", "q2x_tetra",
+                     "q2x_leaf_reduce"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(so):
+    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_no_cpu_fallback(so):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2107_10942_gb300 as q
+    with pytest.raises(q.Q2XError) as ei:
+        q.Plan(8)
+    assert ei.value.status == 3  # Q2X_ERR_CUDA
+
+
+def test_null_plan_is_an_argument_error(so):
+    so.q2x_segments.restype = ctypes.c_int
+    st = so.q2x_segments(None, ctypes.c_int64(0), ctypes.c_int64(0), None, None, None, ctypes.c_int64(0), None,
+                         None, None, None, None, 0)
+    assert st == 1
+    so.q2x_last_error.restype = ctypes.c_char_p
+    so.q2x_last_error.argtypes = [ctypes.c_void_p]
+    assert so.q2x_last_error(None)  # a message is recorded
