@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Q2X benchmark: element-moments/s of the Q2X step on GB300.
+
+Workload: the SH-perturbed level-7 icosphere (327,680 flat triangles,
+163,842 vertices), linear per-vertex density U[-1,1], uniform depth-5 octree
+over [-1.125, 1.125]^3, p = 12, single + double layer in one pass, FP64
+coefficients out.  A step is one Q2X call over the whole mesh; the metric
+counts (p+1)^2 moments per element per output layer.  The FP32-mixed path is
+measured on the same workload and reported beside it, each with its error
+against the FP64 oracle on the CPU-baseline sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 launch with torch.distributed.run: every rank processes its own
+replica of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "Q2X element-moments/s (elems*(p+1)^2), FP32-mixed vs FP64 at stated rel. error"
+UNIT = "element-moments/s"
+LEVEL, DEPTH, P = 7, 5, 12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    return W.cfg_sphere_linear(level=LEVEL, depth=DEPTH, p=P)
+
+
+def workload_name(prob):
+    return "sphere-L%d-linear-depth%d: %d triangles, %d vertices, %d leaves, p=%d, single+double layer" % (
+        LEVEL, DEPTH, prob["idx"].shape[1], prob["vxyz"].shape[1], prob["leaf_c"].shape[1], P)
+
+
+def moments_per_step(prob, layers=2):
+    return layers * prob["idx"].shape[1] * (P + 1) ** 2
+
+
+# ------------------------------------------------------------ oracle (CPU)
+
+def sample_leaves(prob, target_elems):
+    """Leaves taken in a fixed seeded order until target_elems elements."""
+    off = prob["leaf_off"]
+    nl = off.shape[0] - 1
+    order = np.random.default_rng(99).permutation(nl)
+    pick, tot = [], 0
+    for L in order:
+        pick.append(int(L))
+        tot += int(off[L + 1] - off[L])
+        if tot >= target_elems:
+            break
+    return np.array(sorted(pick))
+
+
+def sub_problem(prob, leaves):
+    off = prob["leaf_off"]
+    idx = np.concatenate([prob["idx"][:, off[L]:off[L + 1]] for L in leaves], axis=1)
+    sizes = np.array([off[L + 1] - off[L] for L in leaves])
+    sub_off = np.zeros(len(leaves) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=sub_off[1:])
+    return dict(vxyz=prob["vxyz"], idx=np.ascontiguousarray(idx), sigma=prob["sigma"], leaf_off=sub_off,
+                leaf_c=np.ascontiguousarray(prob["leaf_c"][:, leaves]), leaf_rho=prob["leaf_rho"][leaves],
+                p=prob["p"])
+
+
+def oracle_run(orc, sub, nthreads=0):
+    s = orc.moments("triangle", sub["vxyz"], sub["idx"], sub["sigma"], P, leaf_off=sub["leaf_off"],
+                    leaf_c=sub["leaf_c"], layer=0, density=1, nthreads=nthreads)
+    d = orc.moments("triangle", sub["vxyz"], sub["idx"], sub["sigma"], P, leaf_off=sub["leaf_off"],
+                    leaf_c=sub["leaf_c"], layer=1, density=1, nthreads=nthreads)
+    return s, d
+
+
+def calibrate_sample(orc, prob, seconds):
+    """Number of elements whose oracle run takes about `seconds`."""
+    probe = sub_problem(prob, sample_leaves(prob, 2000))
+    t0 = time.perf_counter()
+    oracle_run(orc, probe)
+    dt = time.perf_counter() - t0
+    per = dt / max(1, probe["idx"].shape[1])
+    return max(200, int(seconds / per))
+
+
+def norm_err(test, ref, rho, layer):
+    """max over leaves of max|dM^| / max|M^_ref| with M^_n^m = M_n^m
+    sqrt((n+|m|)!(n-|m|)!) / rho^n (double layer: / (n rho^{n-1}))."""
+    worst = 0.0
+    for L in range(ref.shape[0]):
+        s = np.zeros((P + 1) ** 2)
+        for n in range(P + 1):
+            for m in range(-n, n + 1):
+                f = math.sqrt(math.factorial(n + abs(m)) * math.factorial(n - abs(m)))
+                s[n * n + n + m] = f / rho[L] ** n if layer == 0 else f / (max(n, 1) * rho[L] ** max(n - 1, 0))
+        den = np.max(np.abs(ref[L] * s))
+        num = np.max(np.abs((test[L] - ref[L]) * s))
+        worst = max(worst, num / den if den > 0 else num)
+    return worst
+
+
+# ------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.proc = None
+        self.uuid = uuid
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/q2x_clocks_%d.csv" % os.getpid()
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, world):
+    import oracle as orc
+    prob = workload()
+    cores = orc.max_threads()
+    if rank != 0:
+        return
+    n = calibrate_sample(orc, prob, max(1.0, args.cpu_seconds / 3))
+    sub = sub_problem(prob, sample_leaves(prob, n))
+    ne = sub["idx"].shape[1]
+    for _ in range(args.warmup):
+        oracle_run(orc, sub)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_run(orc, sub)
+    dt = (time.perf_counter() - t0) / args.steps
+    val = 2 * ne * (P + 1) ** 2 / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(prob), "sample_elements": ne},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d of %d triangles (whole leaves), single+double layer, FP64 Gauss "
+                                       "quadrature, OpenMP" % (ne, prob["idx"].shape[1])},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ our arm
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_2107_10942_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    import paper_2107_10942_gb300 as q
+    from paper_2107_10942_gb300.q2x import problem_to_device
+    from paper_2107_10942_gb300.roofline import PEAK_FP32_FLOPS, PEAK_FP64_FLOPS, element_flops
+
+    prob = workload()
+    d = problem_to_device(prob, dev)
+    n_elem = prob["idx"].shape[1]
+    nc = (P + 1) ** 2
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    outs = {}
+
+    def step(plan, cs, cd):
+        plan.triangles(d["vxyz"], d["idx"], d["sigma"], d["leaf_off"], d["leaf_c"], d["leaf_rho"], None,
+                       density="linear", single=True, double=True, coef_single=cs, coef_double=cd)
+
+    def timed(prec):
+        plan = q.Plan(P, precision=prec)
+        cs = torch.empty((prob["leaf_c"].shape[1], nc), dtype=torch.float64, device=dev)
+        cd = torch.empty_like(cs)
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step(plan, cs, cd)
+        plan.sync()
+        plan.set_kernel_timing(True)
+        plan.kernel_timing()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        launches0 = plan.launch_count()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))  # L2 flush between timed steps (outside the events)
+            evs[k][0].record(stream)
+            step(plan, cs, cd)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        plan.sync()
+        launches = plan.launch_count() - launches0
+        ms_steps = [a.elapsed_time(b) for a, b in evs]
+        kms, kn = plan.kernel_timing()
+        plan.set_kernel_timing(False)
+        ms = sum(ms_steps) / len(ms_steps)
+        if dist:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        outs[prec] = (cs.cpu().numpy(), cd.cpu().numpy())
+        return dict(ms=ms, kernel_ms=kms / max(kn, 1), launches=launches, plan=plan)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clk = ClockSampler(uuid) if rank == 0 else None
+    if clk:
+        clk.start()
+    r64 = timed("fp64")
+    clocks = clk.stop() if clk else None
+    r32 = timed("fp32")
+
+    # ---- end to end through the public API with host buffers
+    host = {k: torch.from_numpy(np.ascontiguousarray(prob[k])).pin_memory()
+            for k in ("vxyz", "idx", "sigma", "leaf_off", "leaf_c", "leaf_rho")}
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    out_s = torch.empty((prob["leaf_c"].shape[1], nc), dtype=torch.float64).pin_memory()
+    out_d = torch.empty_like(out_s).pin_memory()
+    d2h = 2 * out_s.numel() * 8
+    plan = q.Plan(P, precision="fp64")
+
+    def e2e_step():
+        g = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+        cs, cd = plan.triangles(g["vxyz"], g["idx"], g["sigma"], g["leaf_off"], g["leaf_c"], g["leaf_rho"], None,
+                                density="linear", single=True, double=True)
+        out_s.copy_(cs, non_blocking=True)
+        out_d.copy_(cd, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.sync()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+        dist.barrier()
+
+    per_step = moments_per_step(prob)
+    value = world * per_step / (r64["ms"] * 1e-3)
+    flops_elem = element_flops("triangle", "linear", ("single", "double"), P)
+    achieved64 = flops_elem * n_elem / (r64["kernel_ms"] * 1e-3)
+    achieved32 = flops_elem * n_elem / (r32["kernel_ms"] * 1e-3)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- CPU baseline: the oracle on a bounded sample, and the GPU errors on it
+    cpu = None
+    errs = {}
+    if not args.no_cpu_baseline and world == 1:
+        import oracle as orc
+        n = calibrate_sample(orc, prob, args.cpu_seconds)
+        leaves = sample_leaves(prob, n)
+        sub = sub_problem(prob, leaves)
+        t0 = time.perf_counter()
+        ref_s, ref_d = oracle_run(orc, sub)
+        dt = time.perf_counter() - t0
+        ne = sub["idx"].shape[1]
+        cpu = {"value": 2 * ne * nc / dt, "unit": UNIT, "cores": orc.max_threads(), "kind": "oracle",
+               "sample": "%d of %d triangles (%d whole leaves), single+double layer, FP64 Gauss quadrature "
+                         "(%d nodes/direction), OpenMP; %.1f s" % (ne, n_elem, len(leaves), (P + 5) // 2, dt)}
+        for prec in ("fp64", "fp32"):
+            cs, cd = outs[prec]
+            errs[prec] = {"single": norm_err(cs[leaves], ref_s, prob["leaf_rho"][leaves], 0),
+                          "double": norm_err(cd[leaves], ref_d, prob["leaf_rho"][leaves], 1)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r64["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(prob), "precision": "fp64", "density": "linear",
+                   "layers": ["single", "double"], "p": P, "n_elem": n_elem,
+                   "moments_per_step": per_step, "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved64 / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved64 / PEAK_FP64_FLOPS, "traffic": None,
+                     "kernel": "q2x_elem_kernel<double,12,TRI,LINEAR>", "kernel_ms": r64["kernel_ms"],
+                     "flops_per_launch": flops_elem * n_elem,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz (recipe FP64 1.25 TF)"},
+        "fp32_mixed": {"value": world * per_step / (r32["ms"] * 1e-3), "ms_per_step": r32["ms"],
+                       "speedup_vs_fp64": r64["ms"] / r32["ms"],
+                       "roofline": {"bound": "alu", "achieved": achieved32 / 1e12, "peak": PEAK_FP32_FLOPS / 1e12,
+                                    "unit": "TFLOP/s", "frac": achieved32 / PEAK_FP32_FLOPS,
+                                    "kernel": "q2x_elem_kernel<float,12,TRI,LINEAR>", "kernel_ms": r32["kernel_ms"],
+                                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}},
+        "errors_vs_oracle": errs or None,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * per_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": r64["launches"],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

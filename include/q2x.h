@@ -51,7 +51,7 @@
  *  - Streams: calls are asynchronous on the plan's stream.  Host-side argument
  *    checks return a status synchronously.  Device-side checks (vertex index
  *    out of range, non-finite input, bad leaf degree, bad leaf offsets) set a
- *    device error word; q2x_sync() (or the next call on the plan) reports it as
+ *    device error word; q2x_sync() reports it as
  *    Q2X_ERR_DEVICE_INPUT and clears it.  Invalid elements contribute zero.
  *  - No CPU fallback: without a usable CUDA device every call fails with
  *    Q2X_ERR_CUDA.  No exception crosses the ABI.
@@ -120,6 +120,17 @@ q2x_status q2x_device_errors(q2x_plan_t plan, uint32_t* bits);
 q2x_status q2x_reserve(q2x_plan_t plan, int64_t n_elem, int64_t n_leaves);
 /* Bytes of device workspace the plan currently holds. */
 int64_t q2x_workspace_bytes(q2x_plan_t plan);
+
+/* Profiling hooks.  q2x_plan_set_kernel_timing(plan, 1) makes the plan
+ * bracket every element-kernel launch with a pair of its own CUDA events on its
+ * stream; q2x_plan_kernel_timing() synchronises the stream, returns the summed
+ * duration (ms) and number of the element-kernel launches timed since the
+ * previous query, and resets both.  q2x_launch_count: number of CUDA kernels
+ * this plan has launched since it was created (all of them: checks, element
+ * kernels, fix-ups, reductions). */
+q2x_status q2x_plan_set_kernel_timing(q2x_plan_t plan, int enable);
+q2x_status q2x_plan_kernel_timing(q2x_plan_t plan, double* total_ms, int64_t* n_launches);
+int64_t q2x_launch_count(q2x_plan_t plan);
 
 /* Segments: K coefficients (Lemma 1, Eqs. (rec10)-(rec11)), constant line
  * density sigma[n_elem]; Jacobian |x2 - x1|. */

@@ -23,6 +23,8 @@ _SIGNATURES = {
     "q2x_plan": [_c.POINTER(_p), _i, _i, _i, _p],
     "q2x_plan_destroy": [_p],
     "q2x_plan_set_stream": [_p, _p],
+    "q2x_plan_set_kernel_timing": [_p, _i],
+    "q2x_plan_kernel_timing": [_p, _c.POINTER(_c.c_double), _c.POINTER(_i64)],
     "q2x_sync": [_p],
     "q2x_device_errors": [_p, _u32p],
     "q2x_reserve": [_p, _i64, _i64],
@@ -58,6 +60,8 @@ def lib():
             L.q2x_last_error.restype = _c.c_char_p
             L.q2x_workspace_bytes.argtypes = [_p]
             L.q2x_workspace_bytes.restype = _c.c_int64
+            L.q2x_launch_count.argtypes = [_p]
+            L.q2x_launch_count.restype = _c.c_int64
             _LIB = L
     return _LIB
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "q2x.h"
 #include "q2x_kernels.cuh"
@@ -57,6 +58,10 @@ struct q2x_plan_s {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     int occ_cache[2][4][kNumBins] = {};
+    int timing = 0;
+    std::vector<cudaEvent_t> ev_pool;                            // idle events
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded pairs
+    int64_t launches = 0;
     std::string last_error;
 };
 
@@ -103,6 +108,18 @@ q2x_status ensure_ws(q2x_plan_t plan, size_t bytes)
         return fail(plan, Q2X_ERR_OOM, "workspace allocation of %zu bytes failed", bytes);
     }
     plan->ws_bytes = bytes;
+    return Q2X_OK;
+}
+
+q2x_status take_event(q2x_plan_t plan, cudaEvent_t* ev)
+{
+    if (!plan->ev_pool.empty()) {
+        *ev = plan->ev_pool.back();
+        plan->ev_pool.pop_back();
+        return Q2X_OK;
+    }
+    cudaError_t e = cudaEventCreate(ev);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "cudaEventCreate");
     return Q2X_OK;
 }
 
@@ -266,6 +283,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     if (leaf_off) {
         const int64_t nb = (n_leaves + 1 + 255) / 256;
         check_leaf_off_kernel<<<(unsigned)nb, 256, 0, plan->stream>>>(leaf_off, n_leaves, n_elem, plan->d_err);
+        plan->launches += 1;
     }
     if (need_rho) {
         int* bits = reinterpret_cast<int*>(ws + slot_bytes + rho_bytes);
@@ -275,6 +293,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
         leaf_rho_kernel<<<(unsigned)((n_elem + 255) / 256), 256, 0, plan->stream>>>(
             n_elem, n_vert, nv, vxyz, vxyz + n_vert, vxyz + 2 * n_vert, idx, n_leaves, leaf_off, leaf_c, bits);
         rho_bits_to_double<<<(unsigned)((n_leaves + 255) / 256), 256, 0, plan->stream>>>(bits, rho, n_leaves);
+        plan->launches += 2;
         leaf_rho = rho;
     }
 
@@ -303,8 +322,20 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     a.err = plan->d_err;
 
     const int grid = (int)((n_ranges + q2x::WARPS_PER_CTA - 1) / q2x::WARPS_PER_CTA);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (plan->timing) {
+        st = take_event(plan, &ev0);
+        if (st == Q2X_OK) st = take_event(plan, &ev1);
+        if (st != Q2X_OK) return st;
+        cudaEventRecord(ev0, plan->stream);
+    }
     e = ke.launch(a, grid, smem, plan->stream);
     if (e != cudaSuccess) return cuda_fail(plan, e, "element kernel launch");
+    if (plan->timing) {
+        cudaEventRecord(ev1, plan->stream);
+        plan->ev_pending.emplace_back(ev0, ev1);
+    }
+    plan->launches += 1;
     if (leaf_off && n_ranges > 1) {
         const int d_out = (kind == q2x::KIND_SEG) ? 1 : (kind == q2x::KIND_TET) ? 3 : (dens == Q2X_DENSITY_LINEAR ? 3 : 2);
         const int64_t nw = n_ranges - 1;
@@ -315,6 +346,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
             q2x::q2x_fixup_kernel<double><<<fgrid, 128, 0, plan->stream>>>(a, kind + 1, d_out, d_out - 1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(plan, e, "fixup kernel launch");
+        plan->launches += 1;
     }
     return Q2X_OK;
 }
@@ -371,6 +403,11 @@ q2x_status q2x_plan_destroy(q2x_plan_t plan)
     cudaStreamSynchronize(plan->stream);
     if (plan->ws) cudaFree(plan->ws);
     if (plan->d_err) cudaFree(plan->d_err);
+    for (cudaEvent_t ev : plan->ev_pool) cudaEventDestroy(ev);
+    for (auto& pr : plan->ev_pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
     if (plan->h_err) cudaFreeHost(plan->h_err);
     delete plan;
     return Q2X_OK;
@@ -382,6 +419,36 @@ q2x_status q2x_plan_set_stream(q2x_plan_t plan, void* cuda_stream)
     plan->stream = static_cast<cudaStream_t>(cuda_stream);
     return Q2X_OK;
 }
+
+q2x_status q2x_plan_set_kernel_timing(q2x_plan_t plan, int enable)
+{
+    if (!plan) return Q2X_ERR_ARG;
+    plan->timing = enable ? 1 : 0;
+    return Q2X_OK;
+}
+
+q2x_status q2x_plan_kernel_timing(q2x_plan_t plan, double* total_ms, int64_t* n_launches)
+{
+    if (!plan || !total_ms || !n_launches) return fail(plan, Q2X_ERR_ARG, "NULL argument");
+    cudaSetDevice(plan->device);
+    cudaError_t e = cudaStreamSynchronize(plan->stream);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "cudaStreamSynchronize");
+    double tot = 0.0;
+    for (auto& pr : plan->ev_pending) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+        if (e != cudaSuccess) return cuda_fail(plan, e, "cudaEventElapsedTime");
+        tot += ms;
+        plan->ev_pool.push_back(pr.first);
+        plan->ev_pool.push_back(pr.second);
+    }
+    *total_ms = tot;
+    *n_launches = (int64_t)plan->ev_pending.size();
+    plan->ev_pending.clear();
+    return Q2X_OK;
+}
+
+int64_t q2x_launch_count(q2x_plan_t plan) { return plan ? plan->launches : -1; }
 
 const char* q2x_last_error(q2x_plan_t plan) { return plan ? plan->last_error.c_str() : g_create_error.c_str(); }
 
@@ -502,6 +569,7 @@ q2x_status q2x_leaf_reduce(q2x_plan_t plan, int64_t n_elem, int p, const double*
         elem, np, n_elem, n_leaves, leaf_off, coef, accumulate);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(plan, e, "leaf_reduce launch");
+    plan->launches += 2;
     return Q2X_OK;
 }
 

@@ -92,6 +92,21 @@ class Plan:
     def workspace_bytes(self) -> int:
         return int(lib().q2x_workspace_bytes(self._h))
 
+    def launch_count(self) -> int:
+        """Kernels this plan has launched so far."""
+        return int(lib().q2x_launch_count(self._h))
+
+    def set_kernel_timing(self, enable: bool = True):
+        """Time every element-kernel launch with the library's own CUDA events."""
+        check(lib().q2x_plan_set_kernel_timing(self._h, int(bool(enable))), self._h)
+
+    def kernel_timing(self):
+        """(total ms, launches) of the element kernels timed since the last query."""
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        check(lib().q2x_plan_kernel_timing(self._h, ctypes.byref(ms), ctypes.byref(n)), self._h)
+        return float(ms.value), int(n.value)
+
     # ------------------------------------------------------------ helpers
     def _leaf_args(self, n_elem, leaf_off, leaf_c, leaf_rho, leaf_p):
         if leaf_off is None:

@@ -1,0 +1,56 @@
+"""Algorithmic operation counts and peaks for the roofline of the Q2X kernels.
+
+The count follows the kernels' formulation of the tilde recursion (Eq. (rec10)
+and its relatives): one level update of (n, m) from the row of degree n-1 is
+
+  m > 0:  re = X (b_r - a_r) + Y (b_i + a_i) - z c_r + s_r
+          im = X (b_i - a_i) - Y (b_r + a_r) - z c_i + s_i
+  m = 0:  re = 2 X b_r + 2 Y b_i - z c_r + s_r
+
+with a = x^{m-1}, b = x^{m+1}, c = x^m of degree n-1.  Only terms whose operand
+exists (|order| <= n-1) are counted: 4 adds + 4 FMAs for the xi/eta pair when
+both a and b exist, 4 FMAs when only a does, 2 FMAs for the z term, 2 FMAs
+for m = 0's eta term; the source rides in the FMA addend.  FMA = 2 flops.
+The leaf reduction adds one flop per element and output column."""
+from __future__ import annotations
+
+# GB300 (recipe figures): 152 SMs, 2070 MHz maximum SM clock; FP32: 128 lanes
+# per SM; FP64 nominal 1.25 TFLOP/s, i.e. 2 FP64 FMA lanes per SM per clock.
+N_SM = 152
+CLOCK_HZ = 2.070e9
+PEAK_FP32_FLOPS = N_SM * 128 * 2 * CLOCK_HZ   # 80.5 TFLOP/s
+PEAK_FP64_FLOPS = N_SM * 2 * 2 * CLOCK_HZ     # 1.26 TFLOP/s
+
+
+def stencil_flops(n: int, m: int) -> int:
+    if n == 0:
+        return 0
+    if m == 0:
+        return (4 if n - 1 >= 1 else 0) + 2
+    has_b = m + 1 <= n - 1
+    has_c = m <= n - 1
+    return (12 if has_b else 8) + (4 if has_c else 0)
+
+
+def level_flops(p: int) -> int:
+    return sum(stencil_flops(n, m) for n in range(p + 1) for m in range(n + 1))
+
+
+def element_flops(kind: str, density: str = "const", layers=("single",), p: int = 12) -> int:
+    """Flops per element of one Q2X pass (recursion + double layer + reduction)."""
+    L = level_flops(p)
+    entries = sum(n + 1 for n in range(p + 1))
+    if kind == "segment":
+        f = 2 * L
+    elif kind == "tetra":
+        f = 4 * L
+    elif density == "const":
+        f = 3 * L
+    else:
+        # 5 levels; E source c2 q + s3 j (1 mul + 1 fma per part) and Iw source
+        # s1 i + E (1 fma per part); m = 0 entries are real
+        f = 5 * L + 6 * entries - 3 * (p + 1) + 4 * entries - 2 * (p + 1) + (p + 1)
+    if "double" in layers:
+        f += L
+    f += len(layers) * (p + 1) ** 2
+    return f
