@@ -168,6 +168,40 @@ q2x_status q2x_tetra(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const doub
                      const int64_t* leaf_off, const double* leaf_c, const double* leaf_rho,
                      const int32_t* leaf_p, double* coef, int accumulate);
 
+/* Triangles without any device allocation.  There is no counterpart in the
+ * paper: this is a deployment variant of q2x_triangles for callers that cannot
+ * call cudaMalloc -- solvers that have handed all device memory to their own
+ * pool, code paths that must never synchronise the device (cudaMalloc and
+ * cudaFree may synchronise), and callers that must not meet an out-of-memory
+ * failure at call time.  It takes no plan: the degree bound, norm, precision
+ * and stream come as arguments; the remaining arguments and layouts are those
+ * of q2x_triangles (leaf mode only: leaf_off is required, and leaf_rho is
+ * required in Q2X_FP32_MIXED).
+ * Scratch: the partial sums of leaves that straddle warp ranges live in one
+ * file-scope device array of Q2X_NOALLOC_SCRATCH_BYTES (16 MiB), which every
+ * GPU that loads the library holds until the process exits.  Each warp range
+ * covers Q2X_NOALLOC_RANGE elements and needs 4 (p_max+1)^2 s bytes
+ * (s = 8 for FP64, 4 for FP32-mixed), so the call accepts
+ *   n_elem <= Q2X_NOALLOC_RANGE * floor(Q2X_NOALLOC_SCRATCH_BYTES / (4 (p_max+1)^2 s))
+ * (e.g. 794,112 triangles at p_max = 12 in FP64) and returns Q2X_ERR_RANGE
+ * above that, having launched nothing.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it: make that
+ * first call before any stream capture.  Every call shares the array; calls
+ * that overlap on the GPU race on it and on the device error word.  Device-side
+ * input checks are not reported by this entry point (invalid elements
+ * contribute zero).  Asynchronous on cuda_stream; no allocation, no
+ * synchronisation. */
+#define Q2X_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define Q2X_NOALLOC_RANGE 256
+q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precision precision,
+                                 void* cuda_stream, int64_t n_elem, int64_t n_vert,
+                                 const double* vxyz, const int32_t* idx, q2x_density density,
+                                 const double* sigma, int64_t n_leaves, const int64_t* leaf_off,
+                                 const double* leaf_c, const double* leaf_rho,
+                                 const int32_t* leaf_p, double* coef_single, double* coef_double,
+                                 int accumulate);
+
 /* Segmented sum of per-element coefficient rows into leaves (Eq. (st4)):
  * coef[L] (+)= sum_{e in leaf L} elem[e], elem double[n_elem * (p+1)^2],
  * coef double[n_leaves * (p+1)^2], leaf_off as above (required).  FP64,

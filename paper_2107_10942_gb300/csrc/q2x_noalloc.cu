@@ -1,0 +1,188 @@
+// q2x_noalloc.cu -- q2x_triangles_noalloc: the triangle Q2X call without any
+// device allocation (declared in include/q2x.h).
+//
+// Some callers cannot call cudaMalloc: solvers that have already handed all
+// device memory to their own pool, code paths that must never synchronise the
+// device (cudaMalloc / cudaFree may do so), and callers that must not meet an
+// out-of-memory failure at call time.  For them this entry point runs the same
+// triangle element kernel and fix-up kernel as q2x_triangles, but keeps the
+// kernel's scratch (the partial sums of leaves that straddle warp ranges) in a
+// fixed file-scope __device__ array instead of a plan workspace.  It takes no
+// plan and allocates nothing: no cudaMalloc, cudaFree or allocating library
+// routine is called.
+//
+// Host code cannot use the array's symbol as a device address, so the first
+// call on each device looks up the array's device address with
+// cudaGetSymbolAddress (with that device current) and caches it; make that
+// first call before any stream capture.
+//
+// Every call on a device shares the one array, which keeps the previous call's
+// contents; the kernels write every scratch entry they read within a call, so
+// nothing needs clearing.  Calls that overlap on the GPU (different streams,
+// or host threads) race on the array and on the device error word.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "q2x.h"
+#include "q2x_kernels.cuh"
+
+Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_TRI, q2x::DENS_CONST)
+Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_TRI, q2x::DENS_LINEAR)
+Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_TRI, q2x::DENS_CONST)
+Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_TRI, q2x::DENS_LINEAR)
+
+namespace {
+
+// Scratch of the no-allocation entry point: every GPU that loads the library
+// holds these bytes until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[Q2X_NOALLOC_SCRATCH_BYTES];
+static __device__ unsigned g_noalloc_err;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+void* g_scratch_ptr[kMaxDevices] = {};
+unsigned* g_err_ptr[kMaxDevices] = {};
+
+using LaunchFn = cudaError_t (*)(const q2x::ElemArgs&, int, size_t, cudaStream_t);
+#define Q2X_NA_ENTRY(T, P, KIND, DENS) &q2x::launch_elem<T, P, KIND, DENS>,
+// [precision: 0 FP64, 1 FP32][density][bin 4, 8, 12, 16, 20]
+const LaunchFn kTri[2][2][5] = {
+    {{Q2X_FOR_BINS(Q2X_NA_ENTRY, double, q2x::KIND_TRI, q2x::DENS_CONST)},
+     {Q2X_FOR_BINS(Q2X_NA_ENTRY, double, q2x::KIND_TRI, q2x::DENS_LINEAR)}},
+    {{Q2X_FOR_BINS(Q2X_NA_ENTRY, float, q2x::KIND_TRI, q2x::DENS_CONST)},
+     {Q2X_FOR_BINS(Q2X_NA_ENTRY, float, q2x::KIND_TRI, q2x::DENS_LINEAR)}},
+};
+
+__global__ void noalloc_check_leaf_off(const int64_t* off, int64_t n_leaves, int64_t n_elem, unsigned* err)
+{
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L > n_leaves) return;
+    const int64_t o = off[L];
+    bool bad = (o < 0 || o > n_elem);
+    if (L == 0 && o != 0) bad = true;
+    if (L == n_leaves && o != n_elem) bad = true;
+    if (L < n_leaves && off[L + 1] < o) bad = true;
+    if (bad) atomicOr(err, Q2X_DEVERR_LEAF_OFF);
+}
+
+// Device addresses of the scratch array and error word on the current device
+// (looked up once per device).
+q2x_status noalloc_setup(int dev, void** scratch, unsigned** err)
+{
+    if (dev < 0 || dev >= kMaxDevices) return Q2X_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* s = nullptr;
+        void* e = nullptr;
+        cudaError_t rc = cudaGetSymbolAddress(&s, g_noalloc_scratch);
+        if (rc != cudaSuccess) {
+            cudaGetLastError();
+            return Q2X_ERR_CUDA;
+        }
+        rc = cudaGetSymbolAddress(&e, g_noalloc_err);
+        if (rc != cudaSuccess) {
+            cudaGetLastError();
+            return Q2X_ERR_CUDA;
+        }
+        g_scratch_ptr[dev] = s;
+        g_err_ptr[dev] = static_cast<unsigned*>(e);
+    }
+    *scratch = g_scratch_ptr[dev];
+    *err = g_err_ptr[dev];
+    return Q2X_OK;
+}
+
+}  // namespace
+
+extern "C" q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precision precision,
+                                            void* cuda_stream, int64_t n_elem, int64_t n_vert,
+                                            const double* vxyz, const int32_t* idx,
+                                            q2x_density density, const double* sigma,
+                                            int64_t n_leaves, const int64_t* leaf_off,
+                                            const double* leaf_c, const double* leaf_rho,
+                                            const int32_t* leaf_p, double* coef_single,
+                                            double* coef_double, int accumulate)
+{
+    if (p_max < 0 || p_max > Q2X_P_MAX) return Q2X_ERR_RANGE;
+    if (norm != Q2X_NORM_COEFF && norm != Q2X_NORM_MOMENT) return Q2X_ERR_ARG;
+    if (precision != Q2X_FP64 && precision != Q2X_FP32_MIXED) return Q2X_ERR_ARG;
+    if (density != Q2X_DENSITY_CONST && density != Q2X_DENSITY_LINEAR) return Q2X_ERR_ARG;
+    if (n_elem < 0 || n_vert < 0 || n_leaves < 0) return Q2X_ERR_ARG;
+    if (!coef_single && !coef_double) return Q2X_ERR_ARG;
+    if (accumulate != 0 && accumulate != 1) return Q2X_ERR_ARG;
+    if (!leaf_off || !leaf_c) return Q2X_ERR_ARG;  // leaf mode only
+    if (precision == Q2X_FP32_MIXED && !leaf_rho) return Q2X_ERR_ARG;
+    if (n_elem > 0 && (!vxyz || !idx || !sigma || n_vert <= 0 || n_leaves <= 0)) return Q2X_ERR_ARG;
+
+    const int prec = (precision == Q2X_FP32_MIXED) ? 1 : 0;
+    const size_t elt = prec ? sizeof(float) : sizeof(double);
+    const int np = (p_max + 1) * (p_max + 1);
+    const int64_t T = Q2X_NOALLOC_RANGE;
+    const int64_t n_ranges = (n_elem + T - 1) / T;
+    if ((size_t)n_ranges * 4 * np * elt > (size_t)Q2X_NOALLOC_SCRATCH_BYTES) return Q2X_ERR_RANGE;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return Q2X_ERR_CUDA;
+    }
+    void* scratch = nullptr;
+    unsigned* err = nullptr;
+    q2x_status st = noalloc_setup(dev, &scratch, &err);
+    if (st != Q2X_OK) return st;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+
+    if (n_elem == 0) {
+        if (!accumulate)
+            for (double* c : {coef_single, coef_double})
+                if (c && cudaMemsetAsync(c, 0, sizeof(double) * (size_t)n_leaves * np, stream) != cudaSuccess)
+                    return Q2X_ERR_CUDA;
+        return Q2X_OK;
+    }
+
+    int bin = -1;
+    const int bins[5] = {4, 8, 12, 16, 20};
+    for (int b = 0; b < 5 && bin < 0; ++b)
+        if (p_max <= bins[b]) bin = b;
+
+    q2x::ElemArgs a;
+    a.n_elem = n_elem;
+    a.n_vert = n_vert;
+    a.vx = vxyz;
+    a.vy = vxyz + n_vert;
+    a.vz = vxyz + 2 * n_vert;
+    a.idx = idx;
+    a.sigma = sigma;
+    a.n_leaves = n_leaves;
+    a.leaf_off = leaf_off;
+    a.leaf_c = leaf_c;
+    a.leaf_rho = leaf_rho;
+    a.leaf_p = leaf_p;
+    a.p_max = p_max;
+    a.np_max = np;
+    a.coef[0] = coef_single;
+    a.coef[1] = coef_double;
+    a.accumulate = accumulate;
+    a.norm = (int)norm;
+    a.T = T;
+    a.n_ranges = n_ranges;
+    a.slots = scratch;
+    a.err = err;
+
+    noalloc_check_leaf_off<<<(unsigned)((n_leaves + 1 + 255) / 256), 256, 0, stream>>>(leaf_off, n_leaves, n_elem, err);
+    const size_t smem = q2x::WARPS_PER_CTA *
+                        (prec ? q2x::warp_smem_bytes<float>(np) : q2x::warp_smem_bytes<double>(np));
+    const int grid = (int)((n_ranges + q2x::WARPS_PER_CTA - 1) / q2x::WARPS_PER_CTA);
+    if (kTri[prec][density][bin](a, grid, smem, stream) != cudaSuccess) return Q2X_ERR_CUDA;
+    if (n_ranges > 1) {
+        const int d_out = (density == Q2X_DENSITY_LINEAR) ? 3 : 2;
+        const int fgrid = (int)((n_ranges - 1 + 3) / 4);
+        if (prec)
+            q2x::q2x_fixup_kernel<float><<<fgrid, 128, 0, stream>>>(a, 2, d_out, d_out - 1);
+        else
+            q2x::q2x_fixup_kernel<double><<<fgrid, 128, 0, stream>>>(a, 2, d_out, d_out - 1);
+        if (cudaGetLastError() != cudaSuccess) return Q2X_ERR_CUDA;
+    }
+    return Q2X_OK;
+}
