@@ -13,14 +13,17 @@
 #include "q2x_kernels.cuh"
 
 // explicit instantiations live in q2x_inst_*.cu
-Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_SEG, q2x::DENS_CONST)
-Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_TRI, q2x::DENS_CONST)
-Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_TRI, q2x::DENS_LINEAR)
-Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_TET, q2x::DENS_CONST)
-Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_SEG, q2x::DENS_CONST)
-Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_TRI, q2x::DENS_CONST)
-Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_TRI, q2x::DENS_LINEAR)
-Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_TET, q2x::DENS_CONST)
+#define Q2X_DECLARE_ALL(T)                                                                         \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_SEG, q2x::DENS_CONST, 1)                                \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_CONST, 1)                                \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_CONST, 2)                                \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_CONST, 3)                                \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_LINEAR, 1)                               \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_LINEAR, 2)                               \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_LINEAR, 3)                               \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TET, q2x::DENS_CONST, 1)
+Q2X_DECLARE_ALL(float)
+Q2X_DECLARE_ALL(double)
 
 namespace {
 
@@ -31,16 +34,27 @@ struct KernelEntry {
 
 constexpr int kNumBins = 5;
 constexpr int kBins[kNumBins] = {4, 8, 12, 16, 20};
+constexpr int kNumCombos = 8;
 
-#define Q2X_ENTRY(T, P, KIND, DENS) {&q2x::launch_elem<T, P, KIND, DENS>, &q2x::occupancy_elem<T, P, KIND, DENS>},
-#define Q2X_ROW(T, KIND, DENS) {Q2X_FOR_BINS(Q2X_ENTRY, T, KIND, DENS)},
-// [precision: 0 FP64, 1 FP32][combo: seg, tri const, tri linear, tet][bin]
-const KernelEntry kTable[2][4][kNumBins] = {
-    {Q2X_ROW(double, q2x::KIND_SEG, q2x::DENS_CONST) Q2X_ROW(double, q2x::KIND_TRI, q2x::DENS_CONST)
-         Q2X_ROW(double, q2x::KIND_TRI, q2x::DENS_LINEAR) Q2X_ROW(double, q2x::KIND_TET, q2x::DENS_CONST)},
-    {Q2X_ROW(float, q2x::KIND_SEG, q2x::DENS_CONST) Q2X_ROW(float, q2x::KIND_TRI, q2x::DENS_CONST)
-         Q2X_ROW(float, q2x::KIND_TRI, q2x::DENS_LINEAR) Q2X_ROW(float, q2x::KIND_TET, q2x::DENS_CONST)},
-};
+#define Q2X_ENTRY(T, P, KIND, DENS, OUTS) \
+    {&q2x::launch_elem<T, P, KIND, DENS, OUTS>, &q2x::occupancy_elem<T, P, KIND, DENS, OUTS>},
+#define Q2X_ROW(T, KIND, DENS, OUTS) {Q2X_FOR_BINS(Q2X_ENTRY, T, KIND, DENS, OUTS)},
+#define Q2X_ROWS(T)                                                                                          \
+    {Q2X_ROW(T, q2x::KIND_SEG, q2x::DENS_CONST, 1) Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_CONST, 1)              \
+         Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_CONST, 2) Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_CONST, 3)          \
+             Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_LINEAR, 1) Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_LINEAR, 2)   \
+                 Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_LINEAR, 3) Q2X_ROW(T, q2x::KIND_TET, q2x::DENS_CONST, 1)}
+// [precision: 0 FP64, 1 FP32][combo][bin]; combos: 0 segments, 1-3 triangles
+// constant density (single, double, both), 4-6 linear density, 7 tetrahedra
+const KernelEntry kTable[2][kNumCombos][kNumBins] = {Q2X_ROWS(double), Q2X_ROWS(float)};
+
+int combo_index(int kind, int dens, bool single, bool dbl)
+{
+    if (kind == q2x::KIND_SEG) return 0;
+    if (kind == q2x::KIND_TET) return 7;
+    const int outs = (single ? 1 : 0) | (dbl ? 2 : 0);
+    return (dens == Q2X_DENSITY_LINEAR ? 4 : 1) + outs - 1;
+}
 
 thread_local std::string g_create_error;
 
@@ -57,7 +71,7 @@ struct q2x_plan_s {
     unsigned* h_err = nullptr;  // pinned
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    int occ_cache[2][4][kNumBins] = {};
+    int occ_cache[2][kNumCombos][kNumBins] = {};
     int timing = 0;
     std::vector<cudaEvent_t> ev_pool;                            // idle events
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded pairs
@@ -251,7 +265,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     }
 
     const int prec = plan->prec;  // 0 FP64, 1 FP32-mixed
-    const int combo = (kind == q2x::KIND_SEG) ? 0 : (kind == q2x::KIND_TET) ? 3 : (dens == Q2X_DENSITY_LINEAR ? 2 : 1);
+    const int combo = combo_index(kind, dens, coef0 != nullptr, kind == q2x::KIND_TRI && coef1 != nullptr);
     const int nv = kind + 2;
     const int bin = bin_index(plan->p_max);
     if (bin < 0) return fail(plan, Q2X_ERR_RANGE, "p_max %d above %d", plan->p_max, Q2X_P_MAX);

@@ -1,0 +1,3 @@
+// Explicit instantiations of the element kernel: f32, triangles-constant-density-double-layer.
+#include "q2x_kernels.cuh"
+Q2X_FOR_BINS(Q2X_INSTANTIATE, float, q2x::KIND_TRI, q2x::DENS_CONST, 2)

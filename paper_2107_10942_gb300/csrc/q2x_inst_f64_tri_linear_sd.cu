@@ -1,0 +1,3 @@
+// Explicit instantiations of the element kernel: f64, triangles-linear-density-both-layers.
+#include "q2x_kernels.cuh"
+Q2X_FOR_BINS(Q2X_INSTANTIATE, double, q2x::KIND_TRI, q2x::DENS_LINEAR, 3)

@@ -2,10 +2,12 @@
 //
 // One warp owns a contiguous range of T = 32*R elements (elements are sorted
 // by leaf).  Each lane runs one element through the paper's recursions in the
-// "tilde" basis (Eqs. (rec10)-(rec15)), row by row in the degree n, with the
-// row of every level held in registers.  After each chunk of degrees the 32
-// lanes stage their coefficients in shared memory and the warp switches to a
-// lane-per-column layout to form segmented (per-leaf) sums over its rows.
+// "tilde" basis (Eqs. (rec10)-(rec15)), degree by degree, with the row of every
+// level held in registers.  All levels of the chain advance together at each
+// order m (level k's source at (n, m) is level k-1's new value at (n, m)), so
+// no source rows are stored.  After each chunk of degrees the 32 lanes stage
+// their coefficients in shared memory and the warp switches to a
+// lane-per-column layout to form per-leaf (segmented) sums over its rows.
 // Leaves that lie wholly inside the warp's range are written directly; the two
 // boundary leaves of a range go to slot partials that q2x_fixup_kernel
 // combines in a fixed order (deterministic, no atomics on the data path).
@@ -28,7 +30,8 @@
 //     (n+2) E_n  = A_x3 E_{n-1}  + s2 q_n + s3 j_n      E = int_edge w h
 //     (n+3) Iw_n = A_x1 Iw_{n-1} + E_n + s1 i_n        Iw = int_T w g
 // so the chain is q, j, E, i, Iw (5 levels), hat weights n!, (n+1)!, (n+2)!,
-// (n+2)!, (n+3)!.
+// (n+2)!, (n+3)!; in hat form E^_n = A E^_{n-1} + (n+1) s2 q^_n + s3 j^_n and
+// Iw^_n = A Iw^_{n-1} + E^_n + s1 i^_n.
 //
 // Double layer (Eq. (rec15)): l~_n = A_nrm i~_{n-1} with the unit normal in
 // place of the vertex (xi = (n_x + i n_y)/2, eta = conj xi, z = n_z); it uses
@@ -44,11 +47,16 @@
 // Scaled local frame: y' = (x - r*) / 2^s with 2^s >= rho_leaf, so |y'| <~ 1;
 // homogeneity of R_n^m (degree n) and the Jacobian (degree dim) give the factor
 // 2^{s (n + dim)} (double layer 2^{s (n + 1)}), applied exactly as an exponent
-// shift when the FP64 coefficient is formed.
+// shift when the FP64 coefficient is formed.  In the FP32 path every FP64
+// quantity is handled with integer operations (exact splitting of the inputs,
+// exponent re-biasing of the outputs), so no FP64 arithmetic runs per moment.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
+#include <utility>
 
 namespace q2x {
 
@@ -56,8 +64,22 @@ enum : int { KIND_SEG = 0, KIND_TRI = 1, KIND_TET = 2 };
 enum : int { DENS_CONST = 0, DENS_LINEAR = 1 };
 
 constexpr int WARPS_PER_CTA = 4;
-constexpr int CHUNK_COLS = 64;  // columns per layer staged per reduction chunk
-constexpr int TILE_LD = 33;     // padded leading dimension of the stage tile
+
+// Stage tile geometry per precision: CHUNK columns per layer, LD = padded
+// row stride (36 floats keeps 16-byte aligned columns for 128-bit loads and
+// conflict-free row writes; 33 doubles for the FP64 tile).
+template <typename T>
+struct KCfg;
+template <>
+struct KCfg<float> {
+    static constexpr int CHUNK = 48;
+    static constexpr int LD = 36;
+};
+template <>
+struct KCfg<double> {
+    static constexpr int CHUNK = 44;
+    static constexpr int LD = 33;
+};
 
 struct ElemArgs {
     int64_t n_elem, n_vert;
@@ -82,36 +104,48 @@ struct ElemArgs {
     unsigned* err;
 };
 
-// ------------------------------------------------------------- small helpers
+// ------------------------------------------------------------- constants
 
-__host__ __device__ constexpr double inv_fact(int n)
-{
-    double f = 1.0;
-    for (int k = 2; k <= n; ++k) f *= (double)k;
-    return 1.0 / f;
-}
+// 1/k! for k = 0..24 in both precisions (compile-time values, no upload).
+#define Q2X_INV_FACT_LIST                                                                          \
+    1.0, 1.0, 0.5, 0.16666666666666666667, 0.041666666666666666667, 0.0083333333333333333333,   \
+        0.0013888888888888888889, 0.00019841269841269841270, 2.4801587301587301587e-05,         \
+        2.7557319223985890653e-06, 2.7557319223985890653e-07, 2.5052108385441718775e-08,        \
+        2.0876756987868098979e-09, 1.6059043836821614599e-10, 1.1470745597729724714e-11,        \
+        7.6471637318198164759e-13, 4.7794773323873852974e-14, 2.8114572543455207632e-15,        \
+        1.5619206968586226462e-16, 8.2206352466243297170e-18, 4.1103176233121648585e-19,        \
+        1.9572941063391261231e-20, 8.8967913924505732867e-22, 3.8681701706306840377e-23,        \
+        1.6117375710961183490e-24
+static __constant__ double c_inv_fact_d[25] = {Q2X_INV_FACT_LIST};
+static __constant__ float c_inv_fact_f[25] = {Q2X_INV_FACT_LIST};
+constexpr double INV_4PI = 0.079577471545947667884;
 
 // chunk of degrees starting at nb for a kernel of capacity P: the longest run
-// of degrees whose column count (2n+1 each) fits CHUNK_COLS; a degree with
-// more columns than that forms a chunk of its own.
-__host__ __device__ constexpr int chunk_end(int nb, int P)
+// of degrees whose column count (2n+1 each) fits C; a degree with more
+// columns than that forms a chunk of its own.
+__host__ __device__ constexpr int chunk_end(int nb, int P, int C)
 {
     int ne = nb + 1;
-    while (ne <= P && (ne + 1) * (ne + 1) - nb * nb <= CHUNK_COLS) ++ne;
+    while (ne <= P && (ne + 1) * (ne + 1) - nb * nb <= C) ++ne;
     return ne;
 }
 
-// exponent s with 2^s >= rho (rho > 0, finite); 0 for rho <= 0 or non-finite
+// ------------------------------------------------------------- bit helpers
+
+// exponent s with 2^s >= rho for finite rho > 0 (0 otherwise), from the bits
 __device__ __forceinline__ int scale_exponent(double rho)
 {
-    if (!(rho > 0.0) || !(rho < 1e300)) return 0;
-    unsigned long long b = (unsigned long long)__double_as_longlong(rho);
-    int e = (int)((b >> 52) & 0x7FF);
-    unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-    if (e == 0) return -1022;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(rho);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if ((b >> 63) || e == 0x7FF || e == 0) return 0;  // negative, non-finite, zero or denormal
     int s = e - 1023;
-    if (mant != 0) s += 1;
-    return max(-120, min(120, s));
+    if (b & 0xFFFFFFFFFFFFFull) s += 1;
+    return max(-100, min(100, s));
+}
+
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return (((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF) != 0x7FF;
 }
 
 // 2^k as a double, by construction
@@ -132,14 +166,14 @@ __device__ __forceinline__ float pow2f(int k)
 // operations only (re-biases the exponent field; FP32 denormals flush to 0).
 __device__ __forceinline__ double f32_scaled_to_f64(float v, int k)
 {
-    unsigned int b = __float_as_uint(v);
-    unsigned int e = (b >> 23) & 0xFF;
+    const unsigned int b = __float_as_uint(v);
+    const unsigned int e = (b >> 23) & 0xFF;
     if (e == 0) return 0.0;
-    unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
     long long de = (long long)e - 127 + 1023 + k;
     if (de <= 0) return 0.0;
     if (de >= 2047) de = 2046;
-    unsigned long long mant = (unsigned long long)(b & 0x7FFFFF) << 29;
+    const unsigned long long mant = (unsigned long long)(b & 0x7FFFFF) << 29;
     return __longlong_as_double((long long)(sign | ((unsigned long long)de << 52) | mant));
 }
 
@@ -149,10 +183,10 @@ __device__ __forceinline__ double f32_scaled_to_f64(float v, int k)
 // hi = lo = 0; a non-finite or too large x sets bad.
 __device__ __forceinline__ void split_f64(double x, float& hi, float& lo, bool& bad)
 {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    int e = (int)((b >> 52) & 0x7FF);
-    unsigned int sign = (unsigned int)(b >> 63) << 31;
-    int ex = e - 1023;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const unsigned int sign = (unsigned int)(b >> 63) << 31;
+    const int ex = e - 1023;
     if (e == 0x7FF || ex > 127) {
         bad = true;
         hi = lo = 0.f;
@@ -164,129 +198,147 @@ __device__ __forceinline__ void split_f64(double x, float& hi, float& lo, bool& 
     }
     hi = __uint_as_float(sign | ((unsigned int)(ex + 127) << 23) |
                          (unsigned int)((b >> 29) & 0x7FFFFF));
-    unsigned int ml = (unsigned int)(b & 0x1FFFFFFFull);
+    const unsigned int ml = (unsigned int)(b & 0x1FFFFFFFull);
     if (ex < -103 || ml == 0) {
         lo = 0.f;
         return;
     }
     // ml * 2^(ex - 52) = (ml * 2^-29) * 2^(ex - 23)
-    float l = __uint2float_rn(ml) * 1.862645149230957e-09f * pow2f(ex - 23);
+    const float l = __uint2float_rn(ml) * 1.862645149230957e-09f * pow2f(ex - 23);
     lo = sign ? -l : l;
 }
 
-// per-column output constant: sign * 1/(n+d)! * (1/4pi for COEFF)
-__device__ __forceinline__ double column_const(int norm, int n, int m_signed, int d)
+// ------------------------------------------------- packed FP32 complex pairs
+// A complex FP32 value (re, im) lives in one 64-bit register pair and is
+// operated on with Blackwell's paired FP32 instructions (add/sub/mul/fma
+// .rn.f32x2), so one tilde-stencil update costs about half the instructions
+// of the scalar form.
+struct cf {
+    unsigned long long v;
+};
+__device__ __forceinline__ cf cf_make(float re, float im)
 {
-    const int m = m_signed < 0 ? -m_signed : m_signed;
-    const bool is_im = m_signed < 0;
-    const int r = m & 3;
-    double s;
-    if (norm == 0) {
-        // (-1)^{n+m} i^m conj(a + ib): Re = {a, b, -a, -b}, Im = {-b, a, b, -a}
-        s = is_im ? ((r == 1 || r == 2) ? 1.0 : -1.0) : ((r <= 1) ? 1.0 : -1.0);
-        if ((n + m) & 1) s = -s;
-        s *= 0.079577471545947667884;  // 1/(4 pi)
-    } else {
-        // i^{-m}(a + ib): Re = {a, b, -a, -b}, Im = {b, -a, -b, a}
-        s = is_im ? ((r == 0 || r == 3) ? 1.0 : -1.0) : ((r <= 1) ? 1.0 : -1.0);
-    }
-    return s * inv_fact(n + d);
+    cf r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(re), "f"(im));
+    return r;
+}
+__device__ __forceinline__ void cf_parts(cf a, float& re, float& im)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(re), "=f"(im) : "l"(a.v));
+}
+__device__ __forceinline__ cf cf_add(cf a, cf b)
+{
+    cf r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ cf cf_sub(cf a, cf b)
+{
+    cf r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ cf cf_mul(cf a, cf b)
+{
+    cf r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ cf cf_fma(cf a, cf b, cf c)
+{
+    cf r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+// (re, im) -> (im, re)
+__device__ __forceinline__ cf cf_swap(cf a)
+{
+    float re, im;
+    cf_parts(a, re, im);
+    return cf_make(im, re);
+}
+// (re, im) -> (-re, im), i.e. -conj
+__device__ __forceinline__ cf cf_negconj(cf a)
+{
+    cf r;
+    r.v = a.v ^ 0x80000000ull;
+    return r;
+}
+__device__ __forceinline__ cf cf_zero()
+{
+    cf r;
+    r.v = 0ull;
+    return r;
 }
 
-// final coefficient from an accumulated sum: acc * cst * 2^shift
-__device__ __forceinline__ double finish_value(float acc, double cst, int shift)
+// One tilde-stencil update in packed form: with a = x^{m-1}, b = x^{m+1},
+// c = x^m of degree n-1 and xi = X + iY,
+//   -xi a + eta b - z c + src = X (b - a) + (Y, -Y) * swap(a + b) - z c + src.
+// For m = 0 pass a = -conj(b): then -xi a + eta b = 2 Re(eta b) (Eq. (rec11))
+// and the imaginary part comes out exactly zero.
+__device__ __forceinline__ cf cf_stencil(cf a, cf b, cf c, cf src, cf X2, cf YmY, cf nZ2)
 {
-    return f32_scaled_to_f64(acc * (float)cst, shift);
-}
-__device__ __forceinline__ double finish_value(double acc, double cst, int shift)
-{
-    return acc * cst * pow2d(shift);
+    const cf d = cf_sub(b, a);
+    const cf sw = cf_swap(cf_add(b, a));
+    cf t = cf_fma(nZ2, c, src);
+    t = cf_fma(X2, d, t);
+    return cf_fma(YmY, sw, t);
 }
 
-// column index -> (n, m)
+// column c -> (n, m), exact for c < 2^20
 __device__ __forceinline__ void col_nm(int c, int& n, int& m)
 {
-    n = (int)sqrtf((float)c);
-    while (n * n > c) --n;
-    while ((n + 1) * (n + 1) <= c) ++n;
+    const float f = (float)c + 0.5f;
+    n = (int)(f * rsqrtf(f));
+    if (n * n > c) --n;
+    if ((n + 1) * (n + 1) <= c) ++n;
     m = c - n * n - n;
 }
 
-// --------------------------------------------------------------- recursion
-
-// One row of the tilde stencil, in place: on entry re/im hold degree n-1
-// (entries >= n are zero), on exit degree n:
-//   x^m <- -xi x^{m-1} + eta x^{m+1} - z x^m + src^m       (m > 0)
-//   x^0 <- 2 Re(eta x^1) - z x^0 + src^0
-// with xi = X + iY, eta = X - iY.
-template <typename T, int P>
-__device__ __forceinline__ void stencil_row(T (&re)[P + 1], T (&im)[P + 1], const int n, const T X,
-                                            const T Y, const T z, const T (&sre)[P + 1],
-                                            const T (&sim)[P + 1])
+// Sign of the packed output of column (n, m) (m < 0: the Im part of order
+// |m|), relative to the staged component (a = Re x~ for even |m|, b = Im x~
+// for odd |m| in the Re column, the other one in the Im column):
+//   COEFF : (-1)^{n+m} i^m conj(a + ib): Re = {a, b, -a, -b}, Im = {-b, a, b, -a}
+//   MOMENT: i^{-m}(a + ib):              Re = {a, b, -a, -b}, Im = {b, -a, -b, a}
+__device__ __forceinline__ bool column_negative(int norm, int n, int m_signed)
 {
-    T pr = T(0), pi = T(0);
-#pragma unroll
-    for (int m = 0; m <= P; ++m) {
-        if (m <= n) {
-            const T cr = re[m], ci = im[m];
-            const T br = (m < P) ? re[(m < P) ? m + 1 : P] : T(0);
-            const T bi = (m < P) ? im[(m < P) ? m + 1 : P] : T(0);
-            T nr, ni;
-            if (m == 0) {
-                nr = fma(T(2) * X, br, sre[0]);
-                nr = fma(T(2) * Y, bi, nr);
-                nr = fma(-z, cr, nr);
-                ni = T(0);
-            } else {
-                const T dr = br - pr, di = bi - pi;
-                const T sr = br + pr, si = bi + pi;
-                nr = fma(X, dr, sre[m]);
-                nr = fma(Y, si, nr);
-                nr = fma(-z, cr, nr);
-                ni = fma(X, di, sim[m]);
-                ni = fma(-Y, sr, ni);
-                ni = fma(-z, ci, ni);
-            }
-            re[m] = nr;
-            im[m] = ni;
-            pr = cr;
-            pi = ci;
-        }
-    }
+    const int m = m_signed < 0 ? -m_signed : m_signed;
+    const int r = m & 3;
+    bool neg;
+    if (m_signed >= 0)
+        neg = r >= 2;
+    else if (norm == 0)
+        neg = !(r == 1 || r == 2);
+    else
+        neg = !(r == 0 || r == 3);
+    if (norm == 0 && ((n + m) & 1)) neg = !neg;
+    return neg;
 }
 
-// Stencil of a row WITHOUT updating it (double layer): value m of degree n
-// goes to f(m, re, im).
-template <typename T, int P, typename F>
-__device__ __forceinline__ void stencil_apply(const T (&re)[P + 1], const T (&im)[P + 1],
-                                              const int n, const T X, const T Y, const T z, F&& f)
+// final coefficient of column (n, m) from a sum acc:
+// acc * sign / (n+d)! (/ 4pi for COEFF) * 2^shift
+__device__ __forceinline__ double finish_value(float acc, int norm, int n, int m, int d, int shift)
 {
-#pragma unroll
-    for (int m = 0; m <= P; ++m) {
-        if (m <= n) {
-            const T cr = re[m], ci = im[m];
-            const T br = (m < P) ? re[(m < P) ? m + 1 : P] : T(0);
-            const T bi = (m < P) ? im[(m < P) ? m + 1 : P] : T(0);
-            const T ar = (m >= 1) ? re[(m >= 1) ? m - 1 : 0] : T(0);
-            const T ai = (m >= 1) ? im[(m >= 1) ? m - 1 : 0] : T(0);
-            T nr, ni;
-            if (m == 0) {
-                nr = T(2) * X * br;
-                nr = fma(T(2) * Y, bi, nr);
-                nr = fma(-z, cr, nr);
-                ni = T(0);
-            } else {
-                const T dr = br - ar, di = bi - ai;
-                const T sr = br + ar, si = bi + ai;
-                nr = X * dr;
-                nr = fma(Y, si, nr);
-                nr = fma(-z, cr, nr);
-                ni = X * di;
-                ni = fma(-Y, sr, ni);
-                ni = fma(-z, ci, ni);
-            }
-            f(m, nr, ni);
-        }
+    float cst = c_inv_fact_f[n + d];
+    if (norm == 0) cst *= (float)INV_4PI;
+    if (column_negative(norm, n, m)) cst = -cst;
+    return f32_scaled_to_f64(acc * cst, shift);
+}
+__device__ __forceinline__ double finish_value(double acc, int norm, int n, int m, int d, int shift)
+{
+    double cst = c_inv_fact_d[n + d];
+    if (norm == 0) cst *= INV_4PI;
+    if (column_negative(norm, n, m)) cst = -cst;
+    return acc * cst * pow2d(shift);
+}
+
+// compile-time loop: f(std::integral_constant<int, I>) for I in [B, E)
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
     }
 }
 
@@ -327,9 +379,8 @@ __device__ __forceinline__ int64_t leaf_lower(const int64_t* __restrict__ off, i
 // complete means the leaf lies wholly in [e_lo, e_hi).
 struct RangeCtx {
     int64_t w, e_lo, e_hi, L_first;
-    int dim;         // 1, 2, 3: power of the scale in the Jacobian
-    int d_out[2];    // hat depth of each layer's output level
-    int shift_n0[2]; // shift = s * (n + shift_n0[layer])
+    int d_out[2];     // hat depth of each layer's output level
+    int shift_n0[2];  // shift = s * (n + shift_n0[layer])
 };
 
 template <typename T>
@@ -339,9 +390,7 @@ __device__ __forceinline__ void flush_value(const ElemArgs& a, const RangeCtx& r
     if (info & 1) {
         int n, m;
         col_nm(c, n, m);
-        const double cst = column_const(a.norm, n, m, rc.d_out[ly]);
-        const int shift = (info >> 1) * (n + rc.shift_n0[ly]);
-        const double v = finish_value(acc, cst, shift);
+        const double v = finish_value(acc, a.norm, n, m, rc.d_out[ly], (info >> 1) * (n + rc.shift_n0[ly]));
         double* dst = a.coef[ly] + (int64_t)L * a.np_max + c;
         if (a.accumulate)
             *dst += v;
@@ -354,76 +403,175 @@ __device__ __forceinline__ void flush_value(const ElemArgs& a, const RangeCtx& r
     }
 }
 
-// Segmented column sums of one staged chunk: columns [c0, c0 + ncols) of each
-// wanted layer, rows 0..nrows-1.  Lane j owns columns j, j+32, ...; its running
-// sum (the open run) lives in accb between chunks and rounds.
-template <typename T>
-__device__ __noinline__ void reduce_chunk(const ElemArgs& a, const RangeCtx& rc, const T* tile,
-                                          T* accb, const long long* rowleaf, const int* rowinfo,
-                                          long long open_leaf, int open_info, int nrows, int c0,
-                                          int ncols, bool want0, bool want1)
+// Sum of col[r0..r1) with four interleaved partial sums (rows r = 4i + t go
+// to partial t), combined as (p0 + p1) + (p2 + p3): a fixed order, so results
+// are reproducible, and four independent dependency chains.
+__device__ __forceinline__ float sum_rows(const float* col, int r0, int r1)
 {
+    float p[4] = {0.f, 0.f, 0.f, 0.f};
+    int r = r0;
+    for (; r < r1 && (r & 3); ++r) p[r & 3] += col[r];
+    for (; r + 4 <= r1; r += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(col + r);
+        p[0] += v.x;
+        p[1] += v.y;
+        p[2] += v.z;
+        p[3] += v.w;
+    }
+    for (; r < r1; ++r) p[r & 3] += col[r];
+    return (p[0] + p[1]) + (p[2] + p[3]);
+}
+__device__ __forceinline__ double sum_rows(const double* col, int r0, int r1)
+{
+    double p[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int r = r0; r < r1; ++r) p[r & 3] += col[r];
+    return (p[0] + p[1]) + (p[2] + p[3]);
+}
+
+// Sum of all 32 rows of a column: independent loads and a pairwise tree.
+__device__ __forceinline__ float sum_rows32(const float* col)
+{
+    float4 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = *reinterpret_cast<const float4*>(col + 4 * i);
+    float s[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s[i] = (v[i].x + v[i].y) + (v[i].z + v[i].w);
+    return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+__device__ __forceinline__ double sum_rows32(const double* col)
+{
+    double s[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s[i] = (col[4 * i] + col[4 * i + 1]) + (col[4 * i + 2] + col[4 * i + 3]);
+    return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+
+// Segmented column sums of one staged chunk: columns [c0, c0 + ncols) of each
+// wanted layer, rows 0..nrows-1.  bmask bit r: row r starts a new run (bit 0:
+// row 0 is not the open run's leaf).  The wanted layers' columns form one index
+// space; lane j owns indices j, j+32, ...; the open run's sum lives in accb
+// between chunks and rounds.  A round that lies in one leaf and fills all 32
+// rows (the common case) takes the fast pairwise path.  All control flow is
+// warp-uniform.
+template <typename T>
+__device__ __forceinline__ void reduce_chunk(const ElemArgs& a, const RangeCtx& rc, const T* tile,
+                                             T* accb, const long long* rowleaf, const int* rowinfo,
+                                             long long open_leaf, int open_info, unsigned bmask,
+                                             int nrows, int c0, int ncols, bool want0, bool want1)
+{
+    constexpr int CH = KCfg<T>::CHUNK, LD = KCfg<T>::LD;
     const int lane = threadIdx.x & 31;
+    const int nlay = (want0 ? 1 : 0) + (want1 ? 1 : 0);
+    const int total = nlay * ncols;
+    const bool fast = (bmask == 0) && (nrows == 32);
 #pragma unroll 1
-    for (int ly = 0; ly < 2; ++ly) {
-        if ((ly == 0 && !want0) || (ly == 1 && !want1)) continue;
-        const T* tl = tile + ly * CHUNK_COLS * TILE_LD;
-        for (int j = lane; j < ncols; j += 32) {
-            const int c = c0 + j;
-            T acc = accb[ly * a.np_max + c];
+    for (int tc = lane; tc < total; tc += 32) {
+        const int second = (tc >= ncols) ? 1 : 0;
+        const int ly = want0 ? second : 1;
+        const int j = tc - second * ncols;
+        const int c = c0 + j;
+        const T* col = tile + (ly * CH + j) * LD;
+        T acc = accb[ly * a.np_max + c];
+        if (fast) {
+            acc += sum_rows32(col);
+        } else {
             long long L = open_leaf;
             int info = open_info;
-            for (int r = 0; r < nrows; ++r) {
-                const long long Lr = rowleaf[r];
-                if (Lr != L) {
-                    flush_value<T>(a, rc, ly, c, acc, L, info);
-                    acc = T(0);
-                    L = Lr;
-                    info = rowinfo[r];
-                }
-                acc += tl[j * TILE_LD + r];
+            unsigned mask = bmask;
+            int r = 0;
+            while (mask) {
+                const int rb = __ffs(mask) - 1;
+                acc += sum_rows(col, r, rb);
+                flush_value<T>(a, rc, ly, c, acc, L, info);
+                acc = T(0);
+                L = rowleaf[rb];
+                info = rowinfo[rb];
+                r = rb;
+                mask &= mask - 1;
             }
-            accb[ly * a.np_max + c] = acc;
+            acc += sum_rows(col, r, nrows);
         }
+        accb[ly * a.np_max + c] = acc;
     }
 }
 
+// ---------------------------------------------------------- chain layout
+
+// Levels of the chain per element kind: the vertex of each level's stencil
+// (0 = x1, 1 = x2, 2 = x3, 3 = x4).  Level k's source is level k-1's new value
+// except for the linear-density chain (see the kernel).
+template <int KIND, int DENS>
+struct Chain;
+template <>
+struct Chain<KIND_SEG, DENS_CONST> {  // q (x2), p (x1)
+    static constexpr int NL = 2, D_OUT = 1;
+    __host__ __device__ static constexpr int vert(int k) { return k == 0 ? 1 : 0; }
+};
+template <>
+struct Chain<KIND_TRI, DENS_CONST> {  // q (x2), j (x3), i (x1)
+    static constexpr int NL = 3, D_OUT = 2;
+    __host__ __device__ static constexpr int vert(int k) { return k == 0 ? 1 : k == 1 ? 2 : 0; }
+};
+template <>
+struct Chain<KIND_TRI, DENS_LINEAR> {  // q (x2), j (x3), E (x3), i (x1), Iw (x1)
+    static constexpr int NL = 5, D_OUT = 3;
+    __host__ __device__ static constexpr int vert(int k) { return k == 0 ? 1 : (k == 1 || k == 2) ? 2 : 0; }
+};
+template <>
+struct Chain<KIND_TET, DENS_CONST> {  // q (x2), j (x3), b (x4), a (x1)
+    static constexpr int NL = 4, D_OUT = 3;
+    __host__ __device__ static constexpr int vert(int k) { return k == 0 ? 1 : k == 1 ? 2 : k == 2 ? 3 : 0; }
+};
+
 // ------------------------------------------------------------------ kernel
 
-// Shared memory per warp: stage tile [2 layers][CHUNK_COLS][TILE_LD] of T,
-// open-run sums [2 layers][np_max] of T, row leaves [32], row infos [32].
+// Shared memory per warp: stage tile [2 layers][CHUNK][LD] of T, open-run sums
+// [2 layers][np_max] of T, row leaves [32], row infos [32].
+// (rounded up to 128 bytes so every warp's tile keeps the 16-byte alignment of
+// the 128-bit column loads)
 template <typename T>
 __host__ __device__ constexpr size_t warp_smem_bytes(int np_max)
 {
-    return sizeof(T) * (size_t)(2 * CHUNK_COLS * TILE_LD + 2 * np_max) + sizeof(long long) * 32 +
-           sizeof(int) * 32;
+    return (sizeof(T) * (size_t)(2 * KCfg<T>::CHUNK * KCfg<T>::LD + 2 * np_max) + sizeof(long long) * 32 +
+            sizeof(int) * 32 + 127) / 128 * 128;
 }
 
-template <typename T, int P, int KIND, int DENS>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32, (sizeof(T) == 8) ? 1 : 2)
+template <typename T, int P>
+__host__ __device__ constexpr int min_ctas()
+{
+    return 2;  // no register spills for the row arrays at P <= 12 (measured best on GB300)
+}
+
+// OUTS: bit 0 = single layer, bit 1 = double layer (triangles); a compile-time
+// choice so each kernel holds exactly one copy of the degree loop.
+template <typename T, int P, int KIND, int DENS, int OUTS>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
     q2x_elem_kernel(const ElemArgs a)
 {
+    using C = Chain<KIND, DENS>;
+    constexpr int NL = C::NL;
+    constexpr int OUT = NL - 1;
+    constexpr int NV = KIND + 2;
+    constexpr int CH = KCfg<T>::CHUNK, LD = KCfg<T>::LD;
+    constexpr bool FP32 = sizeof(T) == 4;
+    constexpr bool LIN = (KIND == KIND_TRI && DENS == DENS_LINEAR);
+
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int64_t w = (int64_t)blockIdx.x * WARPS_PER_CTA + wib;
     if (w >= a.n_ranges) return;
 
-    constexpr bool FP32 = sizeof(T) == 4;
-    constexpr int NV = KIND + 2;
-    // hat depth of the single-layer output level; the double layer is formed
-    // from row n-1 of that level, one factorial lower
-    constexpr int D_OUT =
-        (KIND == KIND_SEG) ? 1 : (KIND == KIND_TET) ? 3 : (DENS == DENS_LINEAR ? 3 : 2);
-
     unsigned char* wsm = smem_raw + (size_t)wib * warp_smem_bytes<T>(a.np_max);
     T* tile = reinterpret_cast<T*>(wsm);
-    T* accb = tile + 2 * CHUNK_COLS * TILE_LD;
+    T* accb = tile + 2 * CH * LD;
     long long* rowleaf = reinterpret_cast<long long*>(accb + 2 * a.np_max);
     int* rowinfo = reinterpret_cast<int*>(rowleaf + 32);
 
-    const bool want0 = a.coef[0] != nullptr;
-    const bool want1 = (KIND == KIND_TRI) && a.coef[1] != nullptr;
+    constexpr bool want0 = (OUTS & 1) != 0;
+    constexpr bool want1 = (KIND == KIND_TRI) && (OUTS & 2) != 0;
     const bool per_elem = a.leaf_off == nullptr;
     const int np = a.np_max;
     const int pw = a.p_max;
@@ -432,9 +580,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (sizeof(T) == 8) ? 1 : 2)
     rc.w = w;
     rc.e_lo = w * a.T;
     rc.e_hi = min(rc.e_lo + a.T, a.n_elem);
-    rc.dim = KIND + 1;
-    rc.d_out[0] = D_OUT;
-    rc.d_out[1] = D_OUT - 1;
+    rc.d_out[0] = C::D_OUT;
+    rc.d_out[1] = C::D_OUT - 1;
     rc.shift_n0[0] = KIND + 1;
     rc.shift_n0[1] = 1;
 
@@ -452,7 +599,9 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (sizeof(T) == 8) ? 1 : 2)
     // zero the coefficients of empty leaves [La, Lb) (overwrite mode)
     auto zero_leaves = [&](int64_t La, int64_t Lb) {
         if (a.accumulate) return;
+#pragma unroll 1
         for (int64_t L = La; L < Lb; ++L)
+#pragma unroll 1
             for (int c = lane; c < np; c += 32) {
                 if (want0) a.coef[0][L * np + c] = 0.0;
                 if (want1) a.coef[1][L * np + c] = 0.0;
@@ -471,6 +620,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (sizeof(T) == 8) ? 1 : 2)
     };
     long long open_leaf = rc.L_first;
     int open_info = leaf_info(rc.L_first);
+    __syncwarp();
 
     for (int64_t e0 = rc.e_lo; e0 < rc.e_hi; e0 += 32) {
         const int64_t e = e0 + lane;
@@ -481,9 +631,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (sizeof(T) == 8) ? 1 : 2)
         int64_t L = open_leaf;
         if (active) L = per_elem ? e : leaf_search(a.leaf_off, open_leaf, L_last, e);
         unsigned errbits = 0;
-        int pL = pw, sexp = 0;
+        int pL = pw, sexp = 0, info = 0;
         double cx = 0.0, cy = 0.0, cz = 0.0;
-        int info = 0;
         if (active) {
             cx = __ldg(a.leaf_c + L);
             cy = __ldg(a.leaf_c + a.n_leaves + L);
@@ -497,19 +646,22 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (sizeof(T) == 8) ? 1 : 2)
             }
             info = leaf_info(L);
             sexp = info >> 1;
-            if (!(isfinite(cx) && isfinite(cy) && isfinite(cz))) errbits |= 2u;
+            if (!(finite_bits(cx) && finite_bits(cy) && finite_bits(cz))) errbits |= 2u;
         }
-        __syncwarp();
+        // run boundaries of this round (warp-uniform mask)
+        const long long Lprev = __shfl_up_sync(0xffffffffu, (long long)L, 1);
+        const bool starts = active && ((lane == 0) ? (L != open_leaf) : (L != Lprev));
+        const unsigned bmask = __ballot_sync(0xffffffffu, starts);
         rowleaf[lane] = (long long)L;
         rowinfo[lane] = info;
         __syncwarp();
-        // empty leaves between consecutive rows
-        if (!per_elem && !a.accumulate) {
-            long long prev = open_leaf;
-            for (int r = 0; r < nrows; ++r) {
-                const long long Lr = rowleaf[r];
-                if (Lr > prev + 1) zero_leaves(prev + 1, Lr);
-                prev = Lr;
+        if (!per_elem && !a.accumulate && bmask) {  // empty leaves between consecutive rows
+            unsigned mk = bmask;
+            while (mk) {
+                const int r = __ffs(mk) - 1;
+                const long long prev = (r == 0) ? open_leaf : rowleaf[r - 1];
+                if (rowleaf[r] > prev + 1) zero_leaves(prev + 1, rowleaf[r]);
+                mk &= mk - 1;
             }
         }
 
@@ -538,15 +690,12 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (sizeof(T) == 8) ? 1 : 2)
                     dens[0] = __ldg(a.sigma + e);
                 }
             }
-            if (!(isfinite(dens[0]) && isfinite(dens[1]) && isfinite(dens[2]))) {
-                errbits |= 2u;
-                bad = true;
-            }
-            s1 = (T)dens[0];
-            s2 = (T)dens[1];
-            s3 = (T)dens[2];
             if constexpr (FP32) {
                 bool nf = false;
+                float lo;
+                split_f64(dens[0], s1, lo, nf);
+                split_f64(dens[1], s2, lo, nf);
+                split_f64(dens[2], s3, lo, nf);
                 float chx, clx, chy, cly, chz, clz;
                 split_f64(cx, chx, clx, nf);
                 split_f64(cy, chy, cly, nf);
@@ -567,13 +716,20 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (sizeof(T) == 8) ? 1 : 2)
                     bad = true;
                 }
             } else {
+                if (!(finite_bits(dens[0]) && finite_bits(dens[1]) && finite_bits(dens[2]))) {
+                    errbits |= 2u;
+                    bad = true;
+                }
+                s1 = dens[0];
+                s2 = dens[1];
+                s3 = dens[2];
                 const double inv = pow2d(-sexp);
 #pragma unroll
                 for (int k = 0; k < NV; ++k) {
                     const double x = active ? __ldg(a.vx + vid[k]) : 0.0;
                     const double y = active ? __ldg(a.vy + vid[k]) : 0.0;
                     const double zz = active ? __ldg(a.vz + vid[k]) : 0.0;
-                    if (!(isfinite(x) && isfinite(y) && isfinite(zz))) {
+                    if (!(finite_bits(x) && finite_bits(y) && finite_bits(zz))) {
                         if (active) errbits |= 2u;
                         bad = true;
                     }
@@ -584,7 +740,12 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (sizeof(T) == 8) ? 1 : 2)
             }
         }
         if (errbits) atomicOr(a.err, errbits);
-        if (bad) pL = -1;
+        if (bad) {  // contributes exact zeros (no NaN can leak into the sums)
+            pL = -1;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) vxl[k] = vyl[k] = vzl[k] = T(0);
+            s1 = s2 = s3 = T(0);
+        }
 
         // ---- Jacobian in the scaled frame, unit normal, seed
         T J, nx = T(0), ny = T(0), nz = T(0);
@@ -608,136 +769,239 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (sizeof(T) == 8) ? 1 : 2)
                 }
             }
         }
-        T seed = (DENS == DENS_LINEAR) ? J : J * s1;
+        T seed = LIN ? J : J * s1;
         if (pL < 0) seed = T(0);
 
-        // chain vertices (half coordinates for xi/eta)
-        const T X1 = T(0.5) * vxl[0], Y1 = T(0.5) * vyl[0], Z1 = vzl[0];
-        const T X2 = T(0.5) * vxl[1], Y2 = T(0.5) * vyl[1], Z2 = vzl[1];
-        const T X3 = T(0.5) * vxl[NV >= 3 ? 2 : 0], Y3 = T(0.5) * vyl[NV >= 3 ? 2 : 0],
-                Z3 = vzl[NV >= 3 ? 2 : 0];
-        const T X4 = T(0.5) * vxl[NV - 1], Y4 = T(0.5) * vyl[NV - 1], Z4 = vzl[NV - 1];
+        // stencil coefficients of each level: X = x/2, Y = y/2, z
+        T LX[NL], LY[NL], LZ[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int v = C::vert(k);
+            LX[k] = T(0.5) * vxl[v];
+            LY[k] = T(0.5) * vyl[v];
+            LZ[k] = vzl[v];
+        }
         const T XN = T(0.5) * nx, YN = T(0.5) * ny, ZN = nz;
 
-        // ---- level rows; degree n-1 on entry of step n
-        // q: q^ (x2) | l1: p^ (segment, x1) or j^ (x3)
-        // l2: i^ (tri const, x1) | E^ (tri linear, x3) | b^ (tet, x4)
-        // l3: i^ (tri linear, x1) | a^ (tet, x1) | l4: Iw^ (tri linear, x1)
-        T q_r[P + 1], q_i[P + 1], l1_r[P + 1], l1_i[P + 1], l2_r[P + 1], l2_i[P + 1];
-        T l3_r[P + 1], l3_i[P + 1], l4_r[P + 1], l4_i[P + 1], s_r[P + 1], s_i[P + 1];
-#pragma unroll
-        for (int m = 0; m <= P; ++m) {
-            q_r[m] = q_i[m] = l1_r[m] = l1_i[m] = l2_r[m] = l2_i[m] = T(0);
-            l3_r[m] = l3_i[m] = l4_r[m] = l4_i[m] = s_r[m] = s_i[m] = T(0);
-        }
-
+        // Degree loop at run time (compact code).  The order loop is unrolled to
+        // the capacity P so every row entry stays in a register; orders above n
+        // are skipped by warp-uniform branches.
         int nb = 0;  // first degree of the chunk being staged
+        if constexpr (FP32) {
+            // ---- FP32: packed complex arithmetic, blocks of MB orders (orders
+            // in (n, block end) are computed but stay exactly zero)
+            constexpr int MB = 2;
+            cf X2[NL], YmY[NL], nZ2[NL];
 #pragma unroll
-        for (int n = 0; n <= P; ++n) {
-            if (n > pw) break;
-            const bool keep = (n <= pL);
-            const int cb = n * n - nb * nb + n;  // tile column of (n, m = 0)
-            // -- double layer from the row of degree n-1 (before advancing it)
-            if constexpr (KIND == KIND_TRI) {
-                if (want1) {
-                    T* t1 = tile + CHUNK_COLS * TILE_LD;
-                    auto put = [&](int m, T vr, T vi) {
-                        if (!keep) vr = vi = T(0);
-                        t1[(cb + m) * TILE_LD + lane] = (m & 1) ? vi : vr;
-                        if (m > 0) t1[(cb - m) * TILE_LD + lane] = (m & 1) ? vr : vi;
-                    };
-                    if constexpr (DENS == DENS_LINEAR)
-                        stencil_apply<T, P>(l4_r, l4_i, n, XN, YN, ZN, put);
-                    else
-                        stencil_apply<T, P>(l2_r, l2_i, n, XN, YN, ZN, put);
-                }
+            for (int k = 0; k < NL; ++k) {
+                X2[k] = cf_make(LX[k], LX[k]);
+                YmY[k] = cf_make(LY[k], -LY[k]);
+                nZ2[k] = cf_make(-LZ[k], -LZ[k]);
             }
-            // -- advance the chain to degree n
-            s_r[0] = (n == 0) ? seed : T(0);
-            stencil_row<T, P>(q_r, q_i, n, X2, Y2, Z2, s_r, s_i);  // q^_n = A_x2 q^_{n-1}
-            s_r[0] = T(0);
-            if constexpr (KIND == KIND_SEG) {
-                stencil_row<T, P>(l1_r, l1_i, n, X1, Y1, Z1, q_r, q_i);  // p^
-            } else {
-                stencil_row<T, P>(l1_r, l1_i, n, X3, Y3, Z3, q_r, q_i);  // j^
-                if constexpr (KIND == KIND_TRI && DENS == DENS_CONST) {
-                    stencil_row<T, P>(l2_r, l2_i, n, X1, Y1, Z1, l1_r, l1_i);  // i^
-                } else if constexpr (KIND == KIND_TRI) {
-                    // E^_n = A_x3 E^_{n-1} + (n+1) s2 q^_n + s3 j^_n
-                    const T c2 = T(n + 1) * s2;
+            const cf XN2 = cf_make(XN, XN), YNm = cf_make(YN, -YN), nZN2 = cf_make(-ZN, -ZN);
+            const cf s1p = cf_make(s1, s1), s3p = cf_make(s3, s3);
+            cf R[NL][P + 1];
 #pragma unroll
-                    for (int m = 0; m <= P; ++m)
-                        if (m <= n) {
-                            s_r[m] = fma(c2, q_r[m], s3 * l1_r[m]);
-                            s_i[m] = fma(c2, q_i[m], s3 * l1_i[m]);
+            for (int k = 0; k < NL; ++k)
+#pragma unroll
+                for (int m = 0; m <= P; ++m) R[k][m] = cf_zero();
+#pragma unroll 1
+            for (int n = 0; n <= pw; ++n) {
+                const bool keep = (n <= pL);
+                float* trow0 = reinterpret_cast<float*>(tile) + (n * n - nb * nb + n) * LD + lane;
+                float* trow1 = trow0 + CH * LD;
+                const float c2f = (float)(n + 1) * (float)s2;
+                const cf c2p = cf_make(c2f, c2f);
+                const cf sd = cf_make((n == 0) ? (float)seed : 0.f, 0.f);
+                cf pa[NL];  // old x^{m-1} of each level
+#pragma unroll
+                for (int mb = 0; mb <= P; mb += MB) {
+                    if (mb <= n) {
+#pragma unroll
+                        for (int m = mb; m < mb + MB && m <= P; ++m) {
+                            const bool st = (m <= n);
+                            cf nw[NL];
+#pragma unroll
+                            for (int k = 0; k < NL; ++k) {
+                                const cf c = R[k][m];
+                                const cf b = (m < P) ? R[k][m < P ? m + 1 : P] : cf_zero();
+                                const cf a = (m == 0) ? cf_negconj(b) : pa[k];
+                                if (KIND == KIND_TRI && k == OUT && want1) {
+                                    // double layer from the output level's row n-1
+                                    cf dl = cf_stencil(a, b, c, cf_zero(), XN2, YNm, nZN2);
+                                    float dr, di;
+                                    cf_parts(dl, dr, di);
+                                    if (!keep) dr = di = 0.f;
+                                    if (st) {
+                                        trow1[m * LD] = (m & 1) ? di : dr;
+                                        if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
+                                    }
+                                }
+                                cf src;
+                                if (k == 0)
+                                    src = (m == 0) ? sd : cf_zero();
+                                else if (LIN && k == 2)
+                                    src = cf_fma(c2p, nw[0], cf_mul(s3p, nw[1]));  // (n+1) s2 q^ + s3 j^
+                                else if (LIN && k == 3)
+                                    src = nw[1];  // i^ <- j^
+                                else if (LIN && k == 4)
+                                    src = cf_fma(s1p, nw[3], nw[2]);  // E^ + s1 i^
+                                else
+                                    src = nw[k > 0 ? k - 1 : 0];
+                                nw[k] = cf_stencil(a, b, c, src, X2[k], YmY[k], nZ2[k]);
+                                pa[k] = c;
+                                R[k][m] = nw[k];
+                            }
+                            if (want0 && st) {
+                                float vr, vi;
+                                cf_parts(nw[OUT], vr, vi);
+                                if (!keep) vr = vi = 0.f;
+                                trow0[m * LD] = (m & 1) ? vi : vr;
+                                if (m > 0) trow0[-m * LD] = (m & 1) ? vr : vi;
+                            }
                         }
-                    stencil_row<T, P>(l2_r, l2_i, n, X3, Y3, Z3, s_r, s_i);
-                    stencil_row<T, P>(l3_r, l3_i, n, X1, Y1, Z1, l1_r, l1_i);  // i^
-                    // Iw^_n = A_x1 Iw^_{n-1} + E^_n + s1 i^_n
-#pragma unroll
-                    for (int m = 0; m <= P; ++m)
-                        if (m <= n) {
-                            s_r[m] = fma(s1, l3_r[m], l2_r[m]);
-                            s_i[m] = fma(s1, l3_i[m], l2_i[m]);
-                        }
-                    stencil_row<T, P>(l4_r, l4_i, n, X1, Y1, Z1, s_r, s_i);
-#pragma unroll
-                    for (int m = 0; m <= P; ++m) s_r[m] = s_i[m] = T(0);
-                } else {
-                    stencil_row<T, P>(l2_r, l2_i, n, X4, Y4, Z4, l1_r, l1_i);  // b^
-                    stencil_row<T, P>(l3_r, l3_i, n, X1, Y1, Z1, l2_r, l2_i);  // a^
-                }
-            }
-            // -- stage the single-layer row of degree n
-            if (want0) {
-#pragma unroll
-                for (int m = 0; m <= P; ++m) {
-                    if (m <= n) {
-                        T vr, vi;
-                        if constexpr (KIND == KIND_SEG) {
-                            vr = l1_r[m];
-                            vi = l1_i[m];
-                        } else if constexpr (KIND == KIND_TRI && DENS == DENS_CONST) {
-                            vr = l2_r[m];
-                            vi = l2_i[m];
-                        } else if constexpr (KIND == KIND_TRI) {
-                            vr = l4_r[m];
-                            vi = l4_i[m];
-                        } else {
-                            vr = l3_r[m];
-                            vi = l3_i[m];
-                        }
-                        if (!keep) vr = vi = T(0);
-                        tile[(cb + m) * TILE_LD + lane] = (m & 1) ? vi : vr;
-                        if (m > 0) tile[(cb - m) * TILE_LD + lane] = (m & 1) ? vr : vi;
                     }
                 }
+                if (n == pw || (n + 2) * (n + 2) - nb * nb > CH) {
+                    __syncwarp();
+                    reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, bmask, nrows,
+                                    nb * nb, (n + 1) * (n + 1) - nb * nb, want0, want1);
+                    __syncwarp();
+                    nb = n + 1;
+                }
             }
-            // -- reduce the chunk when it is complete (chunk ends are compile-time;
-            //    a run-time p_max below P ends the last chunk early)
-            const int ne = chunk_end(nb, P);
-            if (n + 1 == ne) {
-                __syncwarp();
-                reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, nrows,
-                                nb * nb, (n + 1) * (n + 1) - nb * nb, want0, want1);
-                __syncwarp();
-                nb = n + 1;
-            } else if (n == pw) {
-                __syncwarp();
-                reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, nrows,
-                                nb * nb, (n + 1) * (n + 1) - nb * nb, want0, want1);
-                __syncwarp();
+        } else {
+            // ---- FP64: scalar arithmetic, exact order bounds; the last two
+            // orders of each degree use specialised bodies without the
+            // neighbours that are known to vanish (b = 0 at m = n-1, b = c = 0
+            // at m = n), so no DFMA is spent on zero operands.
+            T Rr[NL][P + 1], Ri[NL][P + 1];
+#pragma unroll
+            for (int k = 0; k < NL; ++k)
+#pragma unroll
+                for (int m = 0; m <= P; ++m) Rr[k][m] = Ri[k][m] = T(0);
+#pragma unroll 1
+            for (int n = 0; n <= pw; ++n) {
+                const bool keep = (n <= pL);
+                T* trow0 = tile + (n * n - nb * nb + n) * LD + lane;
+                T* trow1 = trow0 + CH * LD;
+                const T c2 = T(n + 1) * s2;
+                const T sd = (n == 0) ? seed : T(0);
+                T pr[NL], pi[NL];
+#pragma unroll
+                for (int k = 0; k < NL; ++k) pr[k] = pi[k] = T(0);
+                // body of order m; HB: neighbour m+1 present, HC: entry m present
+                auto body = [&](auto m_c, auto hb_c, auto hc_c) {
+                    constexpr int m = decltype(m_c)::value;
+                    constexpr bool HB = decltype(hb_c)::value && (m < P);
+                    constexpr bool HC = decltype(hc_c)::value;
+                    T nr[NL], ni[NL];
+#pragma unroll
+                    for (int k = 0; k < NL; ++k) {
+                        const T cr = HC ? Rr[k][m] : T(0), ci = HC ? Ri[k][m] : T(0);
+                        const T br = HB ? Rr[k][m < P ? m + 1 : P] : T(0);
+                        const T bi = HB ? Ri[k][m < P ? m + 1 : P] : T(0);
+                        if (KIND == KIND_TRI && k == OUT && want1) {
+                            T dr = T(0), di = T(0);
+                            if (m == 0) {
+                                if (HB) dr = fma(T(2) * XN, br, fma(T(2) * YN, bi, dr));
+                                if (HC) dr = fma(-ZN, cr, dr);
+                            } else {
+                                if (HB) {
+                                    dr = fma(XN, br - pr[k], fma(YN, bi + pi[k], dr));
+                                    di = fma(XN, bi - pi[k], fma(-YN, br + pr[k], di));
+                                } else {
+                                    dr = fma(-XN, pr[k], fma(YN, pi[k], dr));
+                                    di = fma(-XN, pi[k], fma(-YN, pr[k], di));
+                                }
+                                if (HC) {
+                                    dr = fma(-ZN, cr, dr);
+                                    di = fma(-ZN, ci, di);
+                                }
+                            }
+                            if (!keep) dr = di = T(0);
+                            trow1[m * LD] = (m & 1) ? di : dr;
+                            if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
+                        }
+                        T sr, si;
+                        if (k == 0) {
+                            sr = (m == 0) ? sd : T(0);
+                            si = T(0);
+                        } else if (LIN && k == 2) {
+                            sr = fma(c2, nr[0], s3 * nr[1]);
+                            si = fma(c2, ni[0], s3 * ni[1]);
+                        } else if (LIN && k == 3) {
+                            sr = nr[1];
+                            si = ni[1];
+                        } else if (LIN && k == 4) {
+                            sr = fma(s1, nr[3], nr[2]);
+                            si = fma(s1, ni[3], ni[2]);
+                        } else {
+                            sr = nr[k > 0 ? k - 1 : 0];
+                            si = ni[k > 0 ? k - 1 : 0];
+                        }
+                        T vr = sr, vi = (m == 0) ? T(0) : si;
+                        if (m == 0) {
+                            if (HB) vr = fma(T(2) * LY[k], bi, fma(T(2) * LX[k], br, vr));
+                            if (HC) vr = fma(-LZ[k], cr, vr);
+                        } else {
+                            if (HB) {
+                                vr = fma(LY[k], bi + pi[k], fma(LX[k], br - pr[k], vr));
+                                vi = fma(-LY[k], br + pr[k], fma(LX[k], bi - pi[k], vi));
+                            } else {
+                                vr = fma(LY[k], pi[k], fma(-LX[k], pr[k], vr));
+                                vi = fma(-LY[k], pr[k], fma(-LX[k], pi[k], vi));
+                            }
+                            if (HC) {
+                                vr = fma(-LZ[k], cr, vr);
+                                vi = fma(-LZ[k], ci, vi);
+                            }
+                        }
+                        nr[k] = vr;
+                        ni[k] = vi;
+                        pr[k] = cr;
+                        pi[k] = ci;
+                        Rr[k][m] = vr;
+                        Ri[k][m] = vi;
+                    }
+                    if (want0) {
+                        T vr = nr[OUT], vi = ni[OUT];
+                        if (!keep) vr = vi = T(0);
+                        trow0[m * LD] = (m & 1) ? vi : vr;
+                        if (m > 0) trow0[-m * LD] = (m & 1) ? vr : vi;
+                    }
+                };
+                using TT = std::integral_constant<bool, true>;
+                using FF = std::integral_constant<bool, false>;
+                static_for<0, P + 1>([&](auto m_c) {
+                    constexpr int m = decltype(m_c)::value;
+                    if (m + 1 < n)
+                        body(m_c, TT{}, TT{});
+                    else if (m + 1 == n)
+                        body(m_c, FF{}, TT{});
+                    else if (m == n)
+                        body(m_c, FF{}, FF{});
+                });
+                if (n == pw || (n + 2) * (n + 2) - nb * nb > CH) {
+                    __syncwarp();
+                    reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, bmask, nrows,
+                                    nb * nb, (n + 1) * (n + 1) - nb * nb, want0, want1);
+                    __syncwarp();
+                    nb = n + 1;
+                }
             }
         }
         // the run open at the end of this round
         open_leaf = rowleaf[nrows - 1];
         open_info = rowinfo[nrows - 1];
+        __syncwarp();
     }
 
     // ---- flush the run left open at the end of the range
-    __syncwarp();
+#pragma unroll 1
     for (int ly = 0; ly < 2; ++ly) {
         if ((ly == 0 && !want0) || (ly == 1 && !want1)) continue;
+#pragma unroll 1
         for (int c = lane; c < np; c += 32)
             flush_value<T>(a, rc, ly, c, accb[ly * np + c], open_leaf, open_info);
     }
@@ -782,9 +1046,8 @@ __global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d1)
             sum += comp;
             int n, m;
             col_nm(c, n, m);
-            const double cst = column_const(a.norm, n, m, ly == 0 ? d0 : d1);
             const int shift = s * (n + (ly == 0 ? dim : 1));
-            const double v = finish_value(sum, cst, shift);
+            const double v = finish_value(sum, a.norm, n, m, ly == 0 ? d0 : d1, shift);
             double* dst = a.coef[ly] + L * np + c;
             if (a.accumulate)
                 *dst += v;
@@ -799,20 +1062,20 @@ __global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d1)
 namespace q2x {
 
 // Launch helpers (explicitly instantiated in q2x_inst_*.cu).
-template <typename T, int P, int KIND, int DENS>
+template <typename T, int P, int KIND, int DENS, int OUTS>
 cudaError_t launch_elem(const ElemArgs& a, int grid, size_t smem, cudaStream_t st)
 {
-    auto k = q2x_elem_kernel<T, P, KIND, DENS>;
+    auto k = q2x_elem_kernel<T, P, KIND, DENS, OUTS>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, WARPS_PER_CTA * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T, int P, int KIND, int DENS>
+template <typename T, int P, int KIND, int DENS, int OUTS>
 cudaError_t occupancy_elem(int* blocks_per_sm, size_t smem)
 {
-    auto k = q2x_elem_kernel<T, P, KIND, DENS>;
+    auto k = q2x_elem_kernel<T, P, KIND, DENS, OUTS>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, WARPS_PER_CTA * 32, smem);
@@ -820,15 +1083,17 @@ cudaError_t occupancy_elem(int* blocks_per_sm, size_t smem)
 
 }  // namespace q2x
 
-#define Q2X_INSTANTIATE(T, P, KIND, DENS)                                                        \
-    template cudaError_t q2x::launch_elem<T, P, KIND, DENS>(const q2x::ElemArgs&, int, size_t,  \
-                                                            cudaStream_t);                       \
-    template cudaError_t q2x::occupancy_elem<T, P, KIND, DENS>(int*, size_t);
+#define Q2X_INSTANTIATE(T, P, KIND, DENS, OUTS)                                                  \
+    template cudaError_t q2x::launch_elem<T, P, KIND, DENS, OUTS>(const q2x::ElemArgs&, int, size_t, \
+                                                                  cudaStream_t);                   \
+    template cudaError_t q2x::occupancy_elem<T, P, KIND, DENS, OUTS>(int*, size_t);
 
-#define Q2X_DECLARE(T, P, KIND, DENS)                                                            \
-    extern template cudaError_t q2x::launch_elem<T, P, KIND, DENS>(const q2x::ElemArgs&, int,   \
-                                                                   size_t, cudaStream_t);        \
-    extern template cudaError_t q2x::occupancy_elem<T, P, KIND, DENS>(int*, size_t);
+#define Q2X_DECLARE(T, P, KIND, DENS, OUTS)                                                      \
+    extern template cudaError_t q2x::launch_elem<T, P, KIND, DENS, OUTS>(const q2x::ElemArgs&, int, \
+                                                                         size_t, cudaStream_t);    \
+    extern template cudaError_t q2x::occupancy_elem<T, P, KIND, DENS, OUTS>(int*, size_t);
 
-// capacity bins of the unrolled kernels
-#define Q2X_FOR_BINS(X, T, KIND, DENS) X(T, 4, KIND, DENS) X(T, 8, KIND, DENS) X(T, 12, KIND, DENS) X(T, 16, KIND, DENS) X(T, 20, KIND, DENS)
+// capacity bins of the kernels
+#define Q2X_FOR_BINS(X, T, KIND, DENS, OUTS)                                                     \
+    X(T, 4, KIND, DENS, OUTS) X(T, 8, KIND, DENS, OUTS) X(T, 12, KIND, DENS, OUTS)               \
+        X(T, 16, KIND, DENS, OUTS) X(T, 20, KIND, DENS, OUTS)

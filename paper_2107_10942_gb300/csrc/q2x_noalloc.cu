@@ -27,10 +27,15 @@
 #include "q2x.h"
 #include "q2x_kernels.cuh"
 
-Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_TRI, q2x::DENS_CONST)
-Q2X_FOR_BINS(Q2X_DECLARE, float, q2x::KIND_TRI, q2x::DENS_LINEAR)
-Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_TRI, q2x::DENS_CONST)
-Q2X_FOR_BINS(Q2X_DECLARE, double, q2x::KIND_TRI, q2x::DENS_LINEAR)
+#define Q2X_NA_DECLARE(T)                                                                          \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_CONST, 1)                                \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_CONST, 2)                                \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_CONST, 3)                                \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_LINEAR, 1)                               \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_LINEAR, 2)                               \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_LINEAR, 3)
+Q2X_NA_DECLARE(float)
+Q2X_NA_DECLARE(double)
 
 namespace {
 
@@ -45,13 +50,13 @@ void* g_scratch_ptr[kMaxDevices] = {};
 unsigned* g_err_ptr[kMaxDevices] = {};
 
 using LaunchFn = cudaError_t (*)(const q2x::ElemArgs&, int, size_t, cudaStream_t);
-#define Q2X_NA_ENTRY(T, P, KIND, DENS) &q2x::launch_elem<T, P, KIND, DENS>,
-// [precision: 0 FP64, 1 FP32][density][bin 4, 8, 12, 16, 20]
-const LaunchFn kTri[2][2][5] = {
-    {{Q2X_FOR_BINS(Q2X_NA_ENTRY, double, q2x::KIND_TRI, q2x::DENS_CONST)},
-     {Q2X_FOR_BINS(Q2X_NA_ENTRY, double, q2x::KIND_TRI, q2x::DENS_LINEAR)}},
-    {{Q2X_FOR_BINS(Q2X_NA_ENTRY, float, q2x::KIND_TRI, q2x::DENS_CONST)},
-     {Q2X_FOR_BINS(Q2X_NA_ENTRY, float, q2x::KIND_TRI, q2x::DENS_LINEAR)}},
+#define Q2X_NA_ENTRY(T, P, KIND, DENS, OUTS) &q2x::launch_elem<T, P, KIND, DENS, OUTS>,
+#define Q2X_NA_ROW(T, DENS, OUTS) {Q2X_FOR_BINS(Q2X_NA_ENTRY, T, q2x::KIND_TRI, DENS, OUTS)},
+#define Q2X_NA_DENS(T, DENS) {Q2X_NA_ROW(T, DENS, 1) Q2X_NA_ROW(T, DENS, 2) Q2X_NA_ROW(T, DENS, 3)},
+// [precision: 0 FP64, 1 FP32][density][layers - 1: single, double, both][bin 4, 8, 12, 16, 20]
+const LaunchFn kTri[2][2][3][5] = {
+    {Q2X_NA_DENS(double, q2x::DENS_CONST) Q2X_NA_DENS(double, q2x::DENS_LINEAR)},
+    {Q2X_NA_DENS(float, q2x::DENS_CONST) Q2X_NA_DENS(float, q2x::DENS_LINEAR)},
 };
 
 __global__ void noalloc_check_leaf_off(const int64_t* off, int64_t n_leaves, int64_t n_elem, unsigned* err)
@@ -174,7 +179,8 @@ extern "C" q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precis
     const size_t smem = q2x::WARPS_PER_CTA *
                         (prec ? q2x::warp_smem_bytes<float>(np) : q2x::warp_smem_bytes<double>(np));
     const int grid = (int)((n_ranges + q2x::WARPS_PER_CTA - 1) / q2x::WARPS_PER_CTA);
-    if (kTri[prec][density][bin](a, grid, smem, stream) != cudaSuccess) return Q2X_ERR_CUDA;
+    const int outs = (coef_single ? 1 : 0) | (coef_double ? 2 : 0);
+    if (kTri[prec][density][outs - 1][bin](a, grid, smem, stream) != cudaSuccess) return Q2X_ERR_CUDA;
     if (n_ranges > 1) {
         const int d_out = (density == Q2X_DENSITY_LINEAR) ? 3 : 2;
         const int fgrid = (int)((n_ranges - 1 + 3) / 4);
