@@ -202,6 +202,58 @@ q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precision precisi
                                  const int32_t* leaf_p, double* coef_single, double* coef_double,
                                  int accumulate);
 
+/* ---- Ragged mixed batch in one persistent launch (CUDA graph) ----------
+ * Several element kinds (segments, triangles, tetrahedra) share one leaf set;
+ * every leaf has its own degree p_leaf <= p_max and its own element counts.
+ * q2x_batch_build (a set-up call: it copies leaf_p and the leaf offsets to the
+ * host, allocates the batch's device memory and synchronises) cuts the work
+ * into tiles of at most tile_elems elements of one kind inside one leaf,
+ * orders them (grouped by kind and degree, most expensive first) and captures
+ * [counter reset, one persistent kernel over all tiles, per-leaf combine] in a
+ * CUDA graph.  q2x_batch_run replays that graph on the plan's stream: coef
+ * (n_leaves x (p_max+1)^2) receives, per leaf, the sum of the single-layer
+ * coefficients of all its elements of all kinds (zero above p_leaf), added in
+ * a fixed order.  The descriptor's device arrays must stay valid and
+ * unchanged in shape while the batch exists; their values may change between
+ * runs.  tile_elems <= 0 picks the default (256).  Triangles may carry
+ * constant or linear density; double layers are not part of a batch.
+ * leaf_rho is required in Q2X_FP32_MIXED. */
+typedef struct {
+    int64_t n_elem;           /* 0: kind absent */
+    int64_t n_vert;
+    const double* vxyz;       /* SoA 3 x n_vert */
+    const int32_t* idx;       /* SoA k x n_elem */
+    const double* sigma;      /* n_elem, or n_vert for linear-density triangles */
+    const int64_t* leaf_off;  /* CSR over the batch's leaves, n_leaves + 1 entries */
+    q2x_density density;      /* triangles only */
+} q2x_batch_elements;
+
+typedef struct {
+    int64_t n_leaves;
+    const double* leaf_c;     /* SoA 3 x n_leaves */
+    const double* leaf_rho;   /* n_leaves */
+    const int32_t* leaf_p;    /* n_leaves, degrees 0..p_max; NULL = p_max */
+    q2x_batch_elements segments, triangles, tetra;
+    double* coef;             /* n_leaves x (p_max+1)^2 */
+    int accumulate;
+} q2x_batch_desc;
+
+typedef struct q2x_batch_s* q2x_batch_t;
+
+q2x_status q2x_batch_build(q2x_plan_t plan, const q2x_batch_desc* desc, int tile_elems, q2x_batch_t* out);
+q2x_status q2x_batch_run(q2x_batch_t batch);
+q2x_status q2x_batch_destroy(q2x_batch_t batch);
+/* Number of tiles and of partial rows of a built batch. */
+q2x_status q2x_batch_info(q2x_batch_t batch, int64_t* n_tiles, int64_t* n_slots, int* tile_elems);
+
+/* Autotuner: build the batch with each candidate tile size, time reps graph
+ * replays of each (CUDA events on the plan's stream, after one warm-up), and
+ * return the fastest candidate in *best and the mean time of every candidate
+ * in ms[n_candidates].  The caller persists the choice (the Python binding
+ * keeps a JSON table keyed by device and workload shape). */
+q2x_status q2x_batch_tune(q2x_plan_t plan, const q2x_batch_desc* desc, const int* candidates,
+                          int n_candidates, int reps, int* best, float* ms);
+
 /* Segmented sum of per-element coefficient rows into leaves (Eq. (st4)):
  * coef[L] (+)= sum_{e in leaf L} elem[e], elem double[n_elem * (p+1)^2],
  * coef double[n_leaves * (p+1)^2], leaf_off as above (required).  FP64,

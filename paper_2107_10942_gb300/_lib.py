@@ -34,7 +34,25 @@ _SIGNATURES = {
     "q2x_triangles_single": [_p, _i64, _i64, _p, _p, _i, _p, _i64, _p, _p, _p, _p, _p, _i],
     "q2x_triangles_double": [_p, _i64, _i64, _p, _p, _i, _p, _i64, _p, _p, _p, _p, _p, _i],
     "q2x_leaf_reduce": [_p, _i64, _i, _p, _i64, _p, _p, _i],
+    "q2x_batch_build": [_p, _p, _i, _c.POINTER(_p)],
+    "q2x_batch_run": [_p],
+    "q2x_batch_destroy": [_p],
+    "q2x_batch_info": [_p, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i)],
+    "q2x_batch_tune": [_p, _p, _p, _i, _i, _c.POINTER(_i), _c.POINTER(_c.c_float)],
 }
+
+
+class BatchElements(_c.Structure):
+    """q2x_batch_elements"""
+    _fields_ = [("n_elem", _i64), ("n_vert", _i64), ("vxyz", _p), ("idx", _p), ("sigma", _p),
+                ("leaf_off", _p), ("density", _i)]
+
+
+class BatchDesc(_c.Structure):
+    """q2x_batch_desc"""
+    _fields_ = [("n_leaves", _i64), ("leaf_c", _p), ("leaf_rho", _p), ("leaf_p", _p),
+                ("segments", BatchElements), ("triangles", BatchElements), ("tetra", BatchElements),
+                ("coef", _p), ("accumulate", _i)]
 
 
 class Q2XError(RuntimeError):

@@ -11,6 +11,7 @@
 
 #include "q2x.h"
 #include "q2x_kernels.cuh"
+#include "q2x_plan.h"
 
 // explicit instantiations live in q2x_inst_*.cu
 #define Q2X_DECLARE_ALL(T)                                                                         \
@@ -60,28 +61,7 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
-struct q2x_plan_s {
-    int p_max = 0;
-    int norm = 0;
-    int prec = 0;
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    int num_sms = 0;
-    unsigned* d_err = nullptr;
-    unsigned* h_err = nullptr;  // pinned
-    void* ws = nullptr;
-    size_t ws_bytes = 0;
-    int occ_cache[2][kNumCombos][kNumBins] = {};
-    int timing = 0;
-    std::vector<cudaEvent_t> ev_pool;                            // idle events
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded pairs
-    int64_t launches = 0;
-    std::string last_error;
-};
-
-namespace {
-
-q2x_status fail(q2x_plan_t plan, q2x_status st, const char* fmt, ...)
+q2x_status q2x_fail(q2x_plan_t plan, q2x_status st, const char* fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -95,10 +75,15 @@ q2x_status fail(q2x_plan_t plan, q2x_status st, const char* fmt, ...)
     return st;
 }
 
-q2x_status cuda_fail(q2x_plan_t plan, cudaError_t e, const char* what)
+q2x_status q2x_cuda_fail(q2x_plan_t plan, cudaError_t e, const char* what)
 {
-    return fail(plan, Q2X_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return q2x_fail(plan, Q2X_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+
+namespace {
+
+#define fail q2x_fail
+#define cuda_fail q2x_cuda_fail
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -106,7 +106,7 @@ struct ElemArgs {
 
 // ------------------------------------------------------------- constants
 
-// 1/k! for k = 0..24 in both precisions (compile-time values, no upload).
+// 1/k! for k = 0..24 (compile-time values, no upload).
 #define Q2X_INV_FACT_LIST                                                                          \
     1.0, 1.0, 0.5, 0.16666666666666666667, 0.041666666666666666667, 0.0083333333333333333333,   \
         0.0013888888888888888889, 0.00019841269841269841270, 2.4801587301587301587e-05,         \
@@ -117,7 +117,6 @@ struct ElemArgs {
         1.9572941063391261231e-20, 8.8967913924505732867e-22, 3.8681701706306840377e-23,        \
         1.6117375710961183490e-24
 static __constant__ double c_inv_fact_d[25] = {Q2X_INV_FACT_LIST};
-static __constant__ float c_inv_fact_f[25] = {Q2X_INV_FACT_LIST};
 constexpr double INV_4PI = 0.079577471545947667884;
 
 // chunk of degrees starting at nb for a kernel of capacity P: the longest run
@@ -317,12 +316,15 @@ __device__ __forceinline__ bool column_negative(int norm, int n, int m_signed)
 
 // final coefficient of column (n, m) from a sum acc:
 // acc * sign / (n+d)! (/ 4pi for COEFF) * 2^shift
+// (FP32 sums are first turned exactly into FP64 and scaled there, so tiny
+// coefficients cannot underflow the FP32 range; this runs once per flushed
+// leaf column, not per moment)
 __device__ __forceinline__ double finish_value(float acc, int norm, int n, int m, int d, int shift)
 {
-    float cst = c_inv_fact_f[n + d];
-    if (norm == 0) cst *= (float)INV_4PI;
+    double cst = c_inv_fact_d[n + d];
+    if (norm == 0) cst *= INV_4PI;
     if (column_negative(norm, n, m)) cst = -cst;
-    return f32_scaled_to_f64(acc * cst, shift);
+    return f32_scaled_to_f64(acc, shift) * cst;
 }
 __device__ __forceinline__ double finish_value(double acc, int norm, int n, int m, int d, int shift)
 {
@@ -527,6 +529,410 @@ struct Chain<KIND_TET, DENS_CONST> {  // q (x2), j (x3), b (x4), a (x1)
 
 // ------------------------------------------------------------------ kernel
 
+// Per-lane element setup: gather the vertices of element e, translate them to
+// the leaf centre (cx, cy, cz) and scale by 2^-sexp (FP32: from exact hi/lo
+// splits of the FP64 inputs), read the densities, and form the stencil
+// coefficients of every level of the chain, the unit normal (triangles) and
+// the seed J * density (linear density: J).  An inactive lane, a bad vertex
+// index or a non-finite input gives an all-zero frame and pL = -1; errbits
+// collects the device error bits.
+template <typename T, int NL>
+struct Frame {
+    T LX[NL], LY[NL], LZ[NL];  // stencil vertex of each level: X = x/2, Y = y/2, z
+    T XN, YN, ZN;              // the same for the unit normal (double layer)
+    T s1, s2, s3;              // densities (vertex values for linear density)
+    T seed;
+};
+
+template <typename T, int KIND, int DENS>
+__device__ __forceinline__ void load_frame(const double* __restrict__ vx, const double* __restrict__ vy,
+                                           const double* __restrict__ vz, const int32_t* __restrict__ idx,
+                                           const double* __restrict__ sigma, int64_t n_elem, int64_t n_vert,
+                                           int64_t e, bool active, double cx, double cy, double cz, int sexp,
+                                           unsigned& errbits, int& pL,
+                                           Frame<T, Chain<KIND, DENS>::NL>& F)
+{
+    using C = Chain<KIND, DENS>;
+    constexpr int NL = C::NL;
+    constexpr int NV = KIND + 2;
+    constexpr bool FP32 = sizeof(T) == 4;
+    constexpr bool LIN = (KIND == KIND_TRI && DENS == DENS_LINEAR);
+    // ---- gather vertices into the scaled local frame
+    T vxl[NV], vyl[NV], vzl[NV];
+    T edge[NV - 1][3];  // x_k - x1 in the scaled frame, k = 2..NV
+    T s1 = T(0), s2 = T(0), s3 = T(0);
+    bool bad = !active;
+    {
+        int64_t vid[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            int64_t v = active ? (int64_t)__ldg(idx + (int64_t)k * n_elem + e) : 0;
+            if (v < 0 || v >= n_vert) {
+                if (active) errbits |= 1u;
+                bad = true;
+                v = 0;
+            }
+            vid[k] = v;
+        }
+        double dens[3] = {0.0, 0.0, 0.0};
+        if (active) {
+            if (DENS == DENS_LINEAR) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) dens[k] = __ldg(sigma + vid[k]);
+            } else {
+                dens[0] = __ldg(sigma + e);
+            }
+        }
+        if constexpr (FP32) {
+            bool nf = false;
+            float lo;
+            float sh[NV][3], sl[NV][3];
+            split_f64(dens[0], s1, lo, nf);
+            split_f64(dens[1], s2, lo, nf);
+            split_f64(dens[2], s3, lo, nf);
+            float chx, clx, chy, cly, chz, clz;
+            split_f64(cx, chx, clx, nf);
+            split_f64(cy, chy, cly, nf);
+            split_f64(cz, chz, clz, nf);
+            const float inv = pow2f(-sexp);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                float hx, lx, hy, ly, hz, lz;
+                split_f64(active ? __ldg(vx + vid[k]) : 0.0, hx, lx, nf);
+                split_f64(active ? __ldg(vy + vid[k]) : 0.0, hy, ly, nf);
+                split_f64(active ? __ldg(vz + vid[k]) : 0.0, hz, lz, nf);
+                vxl[k] = ((hx - chx) + (lx - clx)) * inv;
+                vyl[k] = ((hy - chy) + (ly - cly)) * inv;
+                vzl[k] = ((hz - chz) + (lz - clz)) * inv;
+                sh[k][0] = hx;
+                sh[k][1] = hy;
+                sh[k][2] = hz;
+                sl[k][0] = lx;
+                sl[k][1] = ly;
+                sl[k][2] = lz;
+            }
+            // edge vectors x_k - x1 from the exact splits: the hi parts of nearby
+            // vertices subtract exactly, so the edges (hence J and the normal)
+            // keep FP32 accuracy relative to the edge length itself
+#pragma unroll
+            for (int k = 1; k < NV; ++k)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) edge[k - 1][d] = ((sh[k][d] - sh[0][d]) + (sl[k][d] - sl[0][d])) * inv;
+            if (nf && active) {
+                errbits |= 2u;
+                bad = true;
+            }
+        } else {
+            if (!(finite_bits(dens[0]) && finite_bits(dens[1]) && finite_bits(dens[2]))) {
+                errbits |= 2u;
+                bad = true;
+            }
+            s1 = dens[0];
+            s2 = dens[1];
+            s3 = dens[2];
+            const double inv = pow2d(-sexp);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const double x = active ? __ldg(vx + vid[k]) : 0.0;
+                const double y = active ? __ldg(vy + vid[k]) : 0.0;
+                const double zz = active ? __ldg(vz + vid[k]) : 0.0;
+                if (!(finite_bits(x) && finite_bits(y) && finite_bits(zz))) {
+                    if (active) errbits |= 2u;
+                    bad = true;
+                }
+                vxl[k] = (x - cx) * inv;
+                vyl[k] = (y - cy) * inv;
+                vzl[k] = (zz - cz) * inv;
+            }
+#pragma unroll
+            for (int k = 1; k < NV; ++k) {
+                edge[k - 1][0] = vxl[k] - vxl[0];
+                edge[k - 1][1] = vyl[k] - vyl[0];
+                edge[k - 1][2] = vzl[k] - vzl[0];
+            }
+        }
+    }
+    if (bad) {  // contributes exact zeros (no NaN can leak into the sums)
+        pL = -1;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) vxl[k] = vyl[k] = vzl[k] = T(0);
+#pragma unroll
+        for (int k = 0; k < NV - 1; ++k) edge[k][0] = edge[k][1] = edge[k][2] = T(0);
+        s1 = s2 = s3 = T(0);
+    }
+
+    // ---- Jacobian in the scaled frame, unit normal, seed
+    T J, nx = T(0), ny = T(0), nz = T(0);
+    {
+        const T ux = edge[0][0], uy = edge[0][1], uz = edge[0][2];
+        if constexpr (KIND == KIND_SEG) {
+            J = sqrt(ux * ux + uy * uy + uz * uz);
+        } else {
+            const T wx = edge[NV >= 3 ? 1 : 0][0], wy = edge[NV >= 3 ? 1 : 0][1], wz = edge[NV >= 3 ? 1 : 0][2];
+            const T cxp = uy * wz - uz * wy, cyp = uz * wx - ux * wz, czp = ux * wy - uy * wx;
+            if constexpr (KIND == KIND_TRI) {
+                J = sqrt(cxp * cxp + cyp * cyp + czp * czp);
+                const T inv = (J > T(0)) ? T(1) / J : T(0);
+                nx = cxp * inv;
+                ny = cyp * inv;
+                nz = czp * inv;
+            } else {
+                const T tx = edge[NV - 2][0], ty = edge[NV - 2][1], tz = edge[NV - 2][2];
+                J = fabs(cxp * tx + cyp * ty + czp * tz);
+            }
+        }
+    }
+    T seed = LIN ? J : J * s1;
+    if (pL < 0) seed = T(0);
+
+    // stencil coefficients of each level: X = x/2, Y = y/2, z
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+        const int v = C::vert(k);
+        F.LX[k] = T(0.5) * vxl[v];
+        F.LY[k] = T(0.5) * vyl[v];
+        F.LZ[k] = vzl[v];
+    }
+    F.XN = T(0.5) * nx;
+    F.YN = T(0.5) * ny;
+    F.ZN = nz;
+    F.s1 = s1;
+    F.s2 = s2;
+    F.s3 = s3;
+    F.seed = seed;
+
+}
+
+// The degree loop of one round: advance every level of the chain from degree
+// 0 to pw (rows in registers; the order loop is unrolled to the capacity P),
+// stage each degree's single- and double-layer values of this lane's element
+// in column order of the stage tile (layer 1 at tile + CHUNK*LD), and call
+// reduce(c0, ncols) whenever a chunk of columns [c0, c0 + ncols) is complete.
+template <typename T, int P, int KIND, int DENS, int OUTS, typename Reduce>
+__device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>& F, int pw, int pL, T* tile,
+                                          int lane, Reduce&& reduce)
+{
+    using C = Chain<KIND, DENS>;
+    constexpr int NL = C::NL;
+    constexpr int OUT = NL - 1;
+    constexpr int CH = KCfg<T>::CHUNK, LD = KCfg<T>::LD;
+    constexpr bool FP32 = sizeof(T) == 4;
+    constexpr bool LIN = (KIND == KIND_TRI && DENS == DENS_LINEAR);
+    constexpr bool want0 = (OUTS & 1) != 0;
+    constexpr bool want1 = (KIND == KIND_TRI) && (OUTS & 2) != 0;
+    const T s1 = F.s1, s2 = F.s2, s3 = F.s3, seed = F.seed;
+    const T XN = F.XN, YN = F.YN, ZN = F.ZN;
+    const T* LX = F.LX;
+    const T* LY = F.LY;
+    const T* LZ = F.LZ;
+    // Degree loop at run time (compact code).  The order loop is unrolled to
+    // the capacity P so every row entry stays in a register; orders above n
+    // are skipped by warp-uniform branches.
+    int nb = 0;  // first degree of the chunk being staged
+    if constexpr (FP32) {
+        // ---- FP32: packed complex arithmetic, blocks of MB orders (orders
+        // in (n, block end) are computed but stay exactly zero)
+        constexpr int MB = 2;
+        cf X2[NL], YmY[NL], nZ2[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            X2[k] = cf_make(LX[k], LX[k]);
+            YmY[k] = cf_make(LY[k], -LY[k]);
+            nZ2[k] = cf_make(-LZ[k], -LZ[k]);
+        }
+        const cf XN2 = cf_make(XN, XN), YNm = cf_make(YN, -YN), nZN2 = cf_make(-ZN, -ZN);
+        const cf s1p = cf_make(s1, s1), s3p = cf_make(s3, s3);
+        cf R[NL][P + 1];
+#pragma unroll
+        for (int k = 0; k < NL; ++k)
+#pragma unroll
+            for (int m = 0; m <= P; ++m) R[k][m] = cf_zero();
+#pragma unroll 1
+        for (int n = 0; n <= pw; ++n) {
+            const bool keep = (n <= pL);
+            float* trow0 = reinterpret_cast<float*>(tile) + (n * n - nb * nb + n) * LD + lane;
+            float* trow1 = trow0 + CH * LD;
+            const float c2f = (float)(n + 1) * (float)s2;
+            const cf c2p = cf_make(c2f, c2f);
+            const cf sd = cf_make((n == 0) ? (float)seed : 0.f, 0.f);
+            cf pa[NL];  // old x^{m-1} of each level
+#pragma unroll
+            for (int mb = 0; mb <= P; mb += MB) {
+                if (mb <= n) {
+#pragma unroll
+                    for (int m = mb; m < mb + MB && m <= P; ++m) {
+                        const bool st = (m <= n);
+                        cf nw[NL];
+#pragma unroll
+                        for (int k = 0; k < NL; ++k) {
+                            const cf c = R[k][m];
+                            const cf b = (m < P) ? R[k][m < P ? m + 1 : P] : cf_zero();
+                            const cf a = (m == 0) ? cf_negconj(b) : pa[k];
+                            if (KIND == KIND_TRI && k == OUT && want1) {
+                                // double layer from the output level's row n-1
+                                cf dl = cf_stencil(a, b, c, cf_zero(), XN2, YNm, nZN2);
+                                float dr, di;
+                                cf_parts(dl, dr, di);
+                                if (!keep) dr = di = 0.f;
+                                if (st) {
+                                    trow1[m * LD] = (m & 1) ? di : dr;
+                                    if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
+                                }
+                            }
+                            cf src;
+                            if (k == 0)
+                                src = (m == 0) ? sd : cf_zero();
+                            else if (LIN && k == 2)
+                                src = cf_fma(c2p, nw[0], cf_mul(s3p, nw[1]));  // (n+1) s2 q^ + s3 j^
+                            else if (LIN && k == 3)
+                                src = nw[1];  // i^ <- j^
+                            else if (LIN && k == 4)
+                                src = cf_fma(s1p, nw[3], nw[2]);  // E^ + s1 i^
+                            else
+                                src = nw[k > 0 ? k - 1 : 0];
+                            nw[k] = cf_stencil(a, b, c, src, X2[k], YmY[k], nZ2[k]);
+                            pa[k] = c;
+                            R[k][m] = nw[k];
+                        }
+                        if (want0 && st) {
+                            float vr, vi;
+                            cf_parts(nw[OUT], vr, vi);
+                            if (!keep) vr = vi = 0.f;
+                            trow0[m * LD] = (m & 1) ? vi : vr;
+                            if (m > 0) trow0[-m * LD] = (m & 1) ? vr : vi;
+                        }
+                    }
+                }
+            }
+            if (n == pw || (n + 2) * (n + 2) - nb * nb > CH) {
+                __syncwarp();
+                reduce(nb * nb, (n + 1) * (n + 1) - nb * nb);
+                __syncwarp();
+                nb = n + 1;
+            }
+        }
+    } else {
+        // ---- FP64: scalar arithmetic, exact order bounds; the last two
+        // orders of each degree use specialised bodies without the
+        // neighbours that are known to vanish (b = 0 at m = n-1, b = c = 0
+        // at m = n), so no DFMA is spent on zero operands.
+        T Rr[NL][P + 1], Ri[NL][P + 1];
+#pragma unroll
+        for (int k = 0; k < NL; ++k)
+#pragma unroll
+            for (int m = 0; m <= P; ++m) Rr[k][m] = Ri[k][m] = T(0);
+#pragma unroll 1
+        for (int n = 0; n <= pw; ++n) {
+            const bool keep = (n <= pL);
+            T* trow0 = tile + (n * n - nb * nb + n) * LD + lane;
+            T* trow1 = trow0 + CH * LD;
+            const T c2 = T(n + 1) * s2;
+            const T sd = (n == 0) ? seed : T(0);
+            T pr[NL], pi[NL];
+#pragma unroll
+            for (int k = 0; k < NL; ++k) pr[k] = pi[k] = T(0);
+            // body of order m; HB: neighbour m+1 present, HC: entry m present
+            auto body = [&](auto m_c, auto hb_c, auto hc_c) {
+                constexpr int m = decltype(m_c)::value;
+                constexpr bool HB = decltype(hb_c)::value && (m < P);
+                constexpr bool HC = decltype(hc_c)::value;
+                T nr[NL], ni[NL];
+#pragma unroll
+                for (int k = 0; k < NL; ++k) {
+                    const T cr = HC ? Rr[k][m] : T(0), ci = HC ? Ri[k][m] : T(0);
+                    const T br = HB ? Rr[k][m < P ? m + 1 : P] : T(0);
+                    const T bi = HB ? Ri[k][m < P ? m + 1 : P] : T(0);
+                    if (KIND == KIND_TRI && k == OUT && want1) {
+                        T dr = T(0), di = T(0);
+                        if (m == 0) {
+                            if (HB) dr = fma(T(2) * XN, br, fma(T(2) * YN, bi, dr));
+                            if (HC) dr = fma(-ZN, cr, dr);
+                        } else {
+                            if (HB) {
+                                dr = fma(XN, br - pr[k], fma(YN, bi + pi[k], dr));
+                                di = fma(XN, bi - pi[k], fma(-YN, br + pr[k], di));
+                            } else {
+                                dr = fma(-XN, pr[k], fma(YN, pi[k], dr));
+                                di = fma(-XN, pi[k], fma(-YN, pr[k], di));
+                            }
+                            if (HC) {
+                                dr = fma(-ZN, cr, dr);
+                                di = fma(-ZN, ci, di);
+                            }
+                        }
+                        if (!keep) dr = di = T(0);
+                        trow1[m * LD] = (m & 1) ? di : dr;
+                        if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
+                    }
+                    T sr, si;
+                    if (k == 0) {
+                        sr = (m == 0) ? sd : T(0);
+                        si = T(0);
+                    } else if (LIN && k == 2) {
+                        sr = fma(c2, nr[0], s3 * nr[1]);
+                        si = fma(c2, ni[0], s3 * ni[1]);
+                    } else if (LIN && k == 3) {
+                        sr = nr[1];
+                        si = ni[1];
+                    } else if (LIN && k == 4) {
+                        sr = fma(s1, nr[3], nr[2]);
+                        si = fma(s1, ni[3], ni[2]);
+                    } else {
+                        sr = nr[k > 0 ? k - 1 : 0];
+                        si = ni[k > 0 ? k - 1 : 0];
+                    }
+                    T vr = sr, vi = (m == 0) ? T(0) : si;
+                    if (m == 0) {
+                        if (HB) vr = fma(T(2) * LY[k], bi, fma(T(2) * LX[k], br, vr));
+                        if (HC) vr = fma(-LZ[k], cr, vr);
+                    } else {
+                        if (HB) {
+                            vr = fma(LY[k], bi + pi[k], fma(LX[k], br - pr[k], vr));
+                            vi = fma(-LY[k], br + pr[k], fma(LX[k], bi - pi[k], vi));
+                        } else {
+                            vr = fma(LY[k], pi[k], fma(-LX[k], pr[k], vr));
+                            vi = fma(-LY[k], pr[k], fma(-LX[k], pi[k], vi));
+                        }
+                        if (HC) {
+                            vr = fma(-LZ[k], cr, vr);
+                            vi = fma(-LZ[k], ci, vi);
+                        }
+                    }
+                    nr[k] = vr;
+                    ni[k] = vi;
+                    pr[k] = cr;
+                    pi[k] = ci;
+                    Rr[k][m] = vr;
+                    Ri[k][m] = vi;
+                }
+                if (want0) {
+                    T vr = nr[OUT], vi = ni[OUT];
+                    if (!keep) vr = vi = T(0);
+                    trow0[m * LD] = (m & 1) ? vi : vr;
+                    if (m > 0) trow0[-m * LD] = (m & 1) ? vr : vi;
+                }
+            };
+            using TT = std::integral_constant<bool, true>;
+            using FF = std::integral_constant<bool, false>;
+            static_for<0, P + 1>([&](auto m_c) {
+                constexpr int m = decltype(m_c)::value;
+                if (m + 1 < n)
+                    body(m_c, TT{}, TT{});
+                else if (m + 1 == n)
+                    body(m_c, FF{}, TT{});
+                else if (m == n)
+                    body(m_c, FF{}, FF{});
+            });
+            if (n == pw || (n + 2) * (n + 2) - nb * nb > CH) {
+                __syncwarp();
+                reduce(nb * nb, (n + 1) * (n + 1) - nb * nb);
+                __syncwarp();
+                nb = n + 1;
+            }
+        }
+    }
+}
+
 // Shared memory per warp: stage tile [2 layers][CHUNK][LD] of T, open-run sums
 // [2 layers][np_max] of T, row leaves [32], row infos [32].
 // (rounded up to 128 bytes so every warp's tile keeps the 16-byte alignment of
@@ -665,332 +1071,14 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
             }
         }
 
-        // ---- gather vertices into the scaled local frame
-        T vxl[NV], vyl[NV], vzl[NV];
-        T s1 = T(0), s2 = T(0), s3 = T(0);
-        bool bad = !active;
-        {
-            int64_t vid[NV];
-#pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                int64_t v = active ? (int64_t)__ldg(a.idx + (int64_t)k * a.n_elem + e) : 0;
-                if (v < 0 || v >= a.n_vert) {
-                    if (active) errbits |= 1u;
-                    bad = true;
-                    v = 0;
-                }
-                vid[k] = v;
-            }
-            double dens[3] = {0.0, 0.0, 0.0};
-            if (active) {
-                if (DENS == DENS_LINEAR) {
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) dens[k] = __ldg(a.sigma + vid[k]);
-                } else {
-                    dens[0] = __ldg(a.sigma + e);
-                }
-            }
-            if constexpr (FP32) {
-                bool nf = false;
-                float lo;
-                split_f64(dens[0], s1, lo, nf);
-                split_f64(dens[1], s2, lo, nf);
-                split_f64(dens[2], s3, lo, nf);
-                float chx, clx, chy, cly, chz, clz;
-                split_f64(cx, chx, clx, nf);
-                split_f64(cy, chy, cly, nf);
-                split_f64(cz, chz, clz, nf);
-                const float inv = pow2f(-sexp);
-#pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    float hx, lx, hy, ly, hz, lz;
-                    split_f64(active ? __ldg(a.vx + vid[k]) : 0.0, hx, lx, nf);
-                    split_f64(active ? __ldg(a.vy + vid[k]) : 0.0, hy, ly, nf);
-                    split_f64(active ? __ldg(a.vz + vid[k]) : 0.0, hz, lz, nf);
-                    vxl[k] = ((hx - chx) + (lx - clx)) * inv;
-                    vyl[k] = ((hy - chy) + (ly - cly)) * inv;
-                    vzl[k] = ((hz - chz) + (lz - clz)) * inv;
-                }
-                if (nf && active) {
-                    errbits |= 2u;
-                    bad = true;
-                }
-            } else {
-                if (!(finite_bits(dens[0]) && finite_bits(dens[1]) && finite_bits(dens[2]))) {
-                    errbits |= 2u;
-                    bad = true;
-                }
-                s1 = dens[0];
-                s2 = dens[1];
-                s3 = dens[2];
-                const double inv = pow2d(-sexp);
-#pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    const double x = active ? __ldg(a.vx + vid[k]) : 0.0;
-                    const double y = active ? __ldg(a.vy + vid[k]) : 0.0;
-                    const double zz = active ? __ldg(a.vz + vid[k]) : 0.0;
-                    if (!(finite_bits(x) && finite_bits(y) && finite_bits(zz))) {
-                        if (active) errbits |= 2u;
-                        bad = true;
-                    }
-                    vxl[k] = (x - cx) * inv;
-                    vyl[k] = (y - cy) * inv;
-                    vzl[k] = (zz - cz) * inv;
-                }
-            }
-        }
+        Frame<T, NL> F;
+        load_frame<T, KIND, DENS>(a.vx, a.vy, a.vz, a.idx, a.sigma, a.n_elem, a.n_vert, e, active, cx, cy, cz, sexp,
+                                  errbits, pL, F);
         if (errbits) atomicOr(a.err, errbits);
-        if (bad) {  // contributes exact zeros (no NaN can leak into the sums)
-            pL = -1;
-#pragma unroll
-            for (int k = 0; k < NV; ++k) vxl[k] = vyl[k] = vzl[k] = T(0);
-            s1 = s2 = s3 = T(0);
-        }
-
-        // ---- Jacobian in the scaled frame, unit normal, seed
-        T J, nx = T(0), ny = T(0), nz = T(0);
-        {
-            const T ux = vxl[1] - vxl[0], uy = vyl[1] - vyl[0], uz = vzl[1] - vzl[0];
-            if constexpr (KIND == KIND_SEG) {
-                J = sqrt(ux * ux + uy * uy + uz * uz);
-            } else {
-                const T wx = vxl[2] - vxl[0], wy = vyl[2] - vyl[0], wz = vzl[2] - vzl[0];
-                const T cxp = uy * wz - uz * wy, cyp = uz * wx - ux * wz, czp = ux * wy - uy * wx;
-                if constexpr (KIND == KIND_TRI) {
-                    J = sqrt(cxp * cxp + cyp * cyp + czp * czp);
-                    const T inv = (J > T(0)) ? T(1) / J : T(0);
-                    nx = cxp * inv;
-                    ny = cyp * inv;
-                    nz = czp * inv;
-                } else {
-                    const T tx = vxl[NV - 1] - vxl[0], ty = vyl[NV - 1] - vyl[0],
-                            tz = vzl[NV - 1] - vzl[0];
-                    J = fabs(cxp * tx + cyp * ty + czp * tz);
-                }
-            }
-        }
-        T seed = LIN ? J : J * s1;
-        if (pL < 0) seed = T(0);
-
-        // stencil coefficients of each level: X = x/2, Y = y/2, z
-        T LX[NL], LY[NL], LZ[NL];
-#pragma unroll
-        for (int k = 0; k < NL; ++k) {
-            const int v = C::vert(k);
-            LX[k] = T(0.5) * vxl[v];
-            LY[k] = T(0.5) * vyl[v];
-            LZ[k] = vzl[v];
-        }
-        const T XN = T(0.5) * nx, YN = T(0.5) * ny, ZN = nz;
-
-        // Degree loop at run time (compact code).  The order loop is unrolled to
-        // the capacity P so every row entry stays in a register; orders above n
-        // are skipped by warp-uniform branches.
-        int nb = 0;  // first degree of the chunk being staged
-        if constexpr (FP32) {
-            // ---- FP32: packed complex arithmetic, blocks of MB orders (orders
-            // in (n, block end) are computed but stay exactly zero)
-            constexpr int MB = 2;
-            cf X2[NL], YmY[NL], nZ2[NL];
-#pragma unroll
-            for (int k = 0; k < NL; ++k) {
-                X2[k] = cf_make(LX[k], LX[k]);
-                YmY[k] = cf_make(LY[k], -LY[k]);
-                nZ2[k] = cf_make(-LZ[k], -LZ[k]);
-            }
-            const cf XN2 = cf_make(XN, XN), YNm = cf_make(YN, -YN), nZN2 = cf_make(-ZN, -ZN);
-            const cf s1p = cf_make(s1, s1), s3p = cf_make(s3, s3);
-            cf R[NL][P + 1];
-#pragma unroll
-            for (int k = 0; k < NL; ++k)
-#pragma unroll
-                for (int m = 0; m <= P; ++m) R[k][m] = cf_zero();
-#pragma unroll 1
-            for (int n = 0; n <= pw; ++n) {
-                const bool keep = (n <= pL);
-                float* trow0 = reinterpret_cast<float*>(tile) + (n * n - nb * nb + n) * LD + lane;
-                float* trow1 = trow0 + CH * LD;
-                const float c2f = (float)(n + 1) * (float)s2;
-                const cf c2p = cf_make(c2f, c2f);
-                const cf sd = cf_make((n == 0) ? (float)seed : 0.f, 0.f);
-                cf pa[NL];  // old x^{m-1} of each level
-#pragma unroll
-                for (int mb = 0; mb <= P; mb += MB) {
-                    if (mb <= n) {
-#pragma unroll
-                        for (int m = mb; m < mb + MB && m <= P; ++m) {
-                            const bool st = (m <= n);
-                            cf nw[NL];
-#pragma unroll
-                            for (int k = 0; k < NL; ++k) {
-                                const cf c = R[k][m];
-                                const cf b = (m < P) ? R[k][m < P ? m + 1 : P] : cf_zero();
-                                const cf a = (m == 0) ? cf_negconj(b) : pa[k];
-                                if (KIND == KIND_TRI && k == OUT && want1) {
-                                    // double layer from the output level's row n-1
-                                    cf dl = cf_stencil(a, b, c, cf_zero(), XN2, YNm, nZN2);
-                                    float dr, di;
-                                    cf_parts(dl, dr, di);
-                                    if (!keep) dr = di = 0.f;
-                                    if (st) {
-                                        trow1[m * LD] = (m & 1) ? di : dr;
-                                        if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
-                                    }
-                                }
-                                cf src;
-                                if (k == 0)
-                                    src = (m == 0) ? sd : cf_zero();
-                                else if (LIN && k == 2)
-                                    src = cf_fma(c2p, nw[0], cf_mul(s3p, nw[1]));  // (n+1) s2 q^ + s3 j^
-                                else if (LIN && k == 3)
-                                    src = nw[1];  // i^ <- j^
-                                else if (LIN && k == 4)
-                                    src = cf_fma(s1p, nw[3], nw[2]);  // E^ + s1 i^
-                                else
-                                    src = nw[k > 0 ? k - 1 : 0];
-                                nw[k] = cf_stencil(a, b, c, src, X2[k], YmY[k], nZ2[k]);
-                                pa[k] = c;
-                                R[k][m] = nw[k];
-                            }
-                            if (want0 && st) {
-                                float vr, vi;
-                                cf_parts(nw[OUT], vr, vi);
-                                if (!keep) vr = vi = 0.f;
-                                trow0[m * LD] = (m & 1) ? vi : vr;
-                                if (m > 0) trow0[-m * LD] = (m & 1) ? vr : vi;
-                            }
-                        }
-                    }
-                }
-                if (n == pw || (n + 2) * (n + 2) - nb * nb > CH) {
-                    __syncwarp();
-                    reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, bmask, nrows,
-                                    nb * nb, (n + 1) * (n + 1) - nb * nb, want0, want1);
-                    __syncwarp();
-                    nb = n + 1;
-                }
-            }
-        } else {
-            // ---- FP64: scalar arithmetic, exact order bounds; the last two
-            // orders of each degree use specialised bodies without the
-            // neighbours that are known to vanish (b = 0 at m = n-1, b = c = 0
-            // at m = n), so no DFMA is spent on zero operands.
-            T Rr[NL][P + 1], Ri[NL][P + 1];
-#pragma unroll
-            for (int k = 0; k < NL; ++k)
-#pragma unroll
-                for (int m = 0; m <= P; ++m) Rr[k][m] = Ri[k][m] = T(0);
-#pragma unroll 1
-            for (int n = 0; n <= pw; ++n) {
-                const bool keep = (n <= pL);
-                T* trow0 = tile + (n * n - nb * nb + n) * LD + lane;
-                T* trow1 = trow0 + CH * LD;
-                const T c2 = T(n + 1) * s2;
-                const T sd = (n == 0) ? seed : T(0);
-                T pr[NL], pi[NL];
-#pragma unroll
-                for (int k = 0; k < NL; ++k) pr[k] = pi[k] = T(0);
-                // body of order m; HB: neighbour m+1 present, HC: entry m present
-                auto body = [&](auto m_c, auto hb_c, auto hc_c) {
-                    constexpr int m = decltype(m_c)::value;
-                    constexpr bool HB = decltype(hb_c)::value && (m < P);
-                    constexpr bool HC = decltype(hc_c)::value;
-                    T nr[NL], ni[NL];
-#pragma unroll
-                    for (int k = 0; k < NL; ++k) {
-                        const T cr = HC ? Rr[k][m] : T(0), ci = HC ? Ri[k][m] : T(0);
-                        const T br = HB ? Rr[k][m < P ? m + 1 : P] : T(0);
-                        const T bi = HB ? Ri[k][m < P ? m + 1 : P] : T(0);
-                        if (KIND == KIND_TRI && k == OUT && want1) {
-                            T dr = T(0), di = T(0);
-                            if (m == 0) {
-                                if (HB) dr = fma(T(2) * XN, br, fma(T(2) * YN, bi, dr));
-                                if (HC) dr = fma(-ZN, cr, dr);
-                            } else {
-                                if (HB) {
-                                    dr = fma(XN, br - pr[k], fma(YN, bi + pi[k], dr));
-                                    di = fma(XN, bi - pi[k], fma(-YN, br + pr[k], di));
-                                } else {
-                                    dr = fma(-XN, pr[k], fma(YN, pi[k], dr));
-                                    di = fma(-XN, pi[k], fma(-YN, pr[k], di));
-                                }
-                                if (HC) {
-                                    dr = fma(-ZN, cr, dr);
-                                    di = fma(-ZN, ci, di);
-                                }
-                            }
-                            if (!keep) dr = di = T(0);
-                            trow1[m * LD] = (m & 1) ? di : dr;
-                            if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
-                        }
-                        T sr, si;
-                        if (k == 0) {
-                            sr = (m == 0) ? sd : T(0);
-                            si = T(0);
-                        } else if (LIN && k == 2) {
-                            sr = fma(c2, nr[0], s3 * nr[1]);
-                            si = fma(c2, ni[0], s3 * ni[1]);
-                        } else if (LIN && k == 3) {
-                            sr = nr[1];
-                            si = ni[1];
-                        } else if (LIN && k == 4) {
-                            sr = fma(s1, nr[3], nr[2]);
-                            si = fma(s1, ni[3], ni[2]);
-                        } else {
-                            sr = nr[k > 0 ? k - 1 : 0];
-                            si = ni[k > 0 ? k - 1 : 0];
-                        }
-                        T vr = sr, vi = (m == 0) ? T(0) : si;
-                        if (m == 0) {
-                            if (HB) vr = fma(T(2) * LY[k], bi, fma(T(2) * LX[k], br, vr));
-                            if (HC) vr = fma(-LZ[k], cr, vr);
-                        } else {
-                            if (HB) {
-                                vr = fma(LY[k], bi + pi[k], fma(LX[k], br - pr[k], vr));
-                                vi = fma(-LY[k], br + pr[k], fma(LX[k], bi - pi[k], vi));
-                            } else {
-                                vr = fma(LY[k], pi[k], fma(-LX[k], pr[k], vr));
-                                vi = fma(-LY[k], pr[k], fma(-LX[k], pi[k], vi));
-                            }
-                            if (HC) {
-                                vr = fma(-LZ[k], cr, vr);
-                                vi = fma(-LZ[k], ci, vi);
-                            }
-                        }
-                        nr[k] = vr;
-                        ni[k] = vi;
-                        pr[k] = cr;
-                        pi[k] = ci;
-                        Rr[k][m] = vr;
-                        Ri[k][m] = vi;
-                    }
-                    if (want0) {
-                        T vr = nr[OUT], vi = ni[OUT];
-                        if (!keep) vr = vi = T(0);
-                        trow0[m * LD] = (m & 1) ? vi : vr;
-                        if (m > 0) trow0[-m * LD] = (m & 1) ? vr : vi;
-                    }
-                };
-                using TT = std::integral_constant<bool, true>;
-                using FF = std::integral_constant<bool, false>;
-                static_for<0, P + 1>([&](auto m_c) {
-                    constexpr int m = decltype(m_c)::value;
-                    if (m + 1 < n)
-                        body(m_c, TT{}, TT{});
-                    else if (m + 1 == n)
-                        body(m_c, FF{}, TT{});
-                    else if (m == n)
-                        body(m_c, FF{}, FF{});
-                });
-                if (n == pw || (n + 2) * (n + 2) - nb * nb > CH) {
-                    __syncwarp();
-                    reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, bmask, nrows,
-                                    nb * nb, (n + 1) * (n + 1) - nb * nb, want0, want1);
-                    __syncwarp();
-                    nb = n + 1;
-                }
-            }
-        }
+        run_chain<T, P, KIND, DENS, OUTS>(F, pw, pL, tile, lane, [&](int c0, int ncols) {
+            reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, bmask, nrows, c0, ncols,
+                            want0, want1);
+        });
         // the run open at the end of this round
         open_leaf = rowleaf[nrows - 1];
         open_info = rowinfo[nrows - 1];

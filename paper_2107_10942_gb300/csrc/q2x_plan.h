@@ -1,0 +1,33 @@
+// q2x_plan.h -- the plan object behind q2x_plan_t (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "q2x.h"
+
+struct q2x_plan_s {
+    int p_max = 0;
+    int norm = 0;
+    int prec = 0;  // 0 FP64, 1 FP32-mixed
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    unsigned* d_err = nullptr;
+    unsigned* h_err = nullptr;  // pinned
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int occ_cache[2][8][5] = {};  // [precision][element combo][capacity bin]
+    int timing = 0;
+    std::vector<cudaEvent_t> ev_pool;                            // idle events
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded pairs
+    int64_t launches = 0;
+    std::string last_error;
+};
+
+// status helpers shared by the library's translation units
+q2x_status q2x_fail(q2x_plan_t plan, q2x_status st, const char* fmt, ...);
+q2x_status q2x_cuda_fail(q2x_plan_t plan, cudaError_t e, const char* what);

@@ -202,3 +202,106 @@ def problem_to_device(prob: dict, device="cuda") -> dict:
         else:
             out[k] = v
     return out
+
+
+class Batch:
+    """A ragged mixed-kind batch (q2x_batch_*): per-leaf degrees, several
+    element kinds summed into the same leaves, run as one CUDA-graph replay.
+
+    kinds: segments / triangles / tetra, each a dict with torch CUDA tensors
+    vxyz (3, n_vert) f64, idx (k, n_elem) i32, sigma f64, leaf_off (n_leaves+1)
+    i64 and, for triangles, density ("const" | "linear"); None to omit.
+    The tensors are referenced, not copied: keep them alive and unchanged in
+    shape while the batch exists."""
+
+    def __init__(self, plan: Plan, leaf_c, leaf_rho=None, leaf_p=None, coef=None, segments=None, triangles=None,
+                 tetra=None, accumulate=False, tile_elems=0):
+        from ._lib import BatchDesc
+        n_leaves = leaf_c.shape[1]
+        _need(leaf_c, torch.float64, "leaf_c", (3, n_leaves))
+        _need(leaf_rho, torch.float64, "leaf_rho", (n_leaves,))
+        _need(leaf_p, torch.int32, "leaf_p", (n_leaves,))
+        self.plan = plan
+        self.coef = plan._out(coef, n_leaves, leaf_c.device, accumulate)
+        self._keep = [leaf_c, leaf_rho, leaf_p, self.coef]
+        d = BatchDesc()
+        d.n_leaves = n_leaves
+        d.leaf_c = leaf_c.data_ptr()
+        d.leaf_rho = leaf_rho.data_ptr() if leaf_rho is not None else None
+        d.leaf_p = leaf_p.data_ptr() if leaf_p is not None else None
+        d.coef = self.coef.data_ptr()
+        d.accumulate = int(bool(accumulate))
+        for name, nv, kd in (("segments", 2, segments), ("triangles", 3, triangles), ("tetra", 4, tetra)):
+            el = getattr(d, name)
+            if kd is None:
+                el.n_elem = 0
+                continue
+            n_vert, n_elem = plan._geom(kd["vxyz"], kd["idx"], nv)
+            dens = _DENS[kd.get("density", "const")] if name == "triangles" else 0
+            _need(kd["sigma"], torch.float64, name + ".sigma", (n_vert if dens == 1 else n_elem,))
+            _need(kd["leaf_off"], torch.int64, name + ".leaf_off", (n_leaves + 1,))
+            el.n_elem, el.n_vert = n_elem, n_vert
+            el.vxyz, el.idx, el.sigma = kd["vxyz"].data_ptr(), kd["idx"].data_ptr(), kd["sigma"].data_ptr()
+            el.leaf_off, el.density = kd["leaf_off"].data_ptr(), dens
+            self._keep += [kd["vxyz"], kd["idx"], kd["sigma"], kd["leaf_off"]]
+        self._desc = d
+        h = ctypes.c_void_p()
+        check(lib().q2x_batch_build(plan.handle, ctypes.byref(d), int(tile_elems), ctypes.byref(h)), plan.handle)
+        self._h = h
+
+    def run(self):
+        """Replay the batch's CUDA graph on the plan's stream (asynchronous)."""
+        check(lib().q2x_batch_run(self._h), self.plan.handle)
+        return self.coef
+
+    def info(self):
+        nt, ns, te = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        check(lib().q2x_batch_info(self._h, ctypes.byref(nt), ctypes.byref(ns), ctypes.byref(te)))
+        return dict(tiles=nt.value, slots=ns.value, tile_elems=te.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().q2x_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def tune(plan: Plan, candidates=(64, 128, 256, 512, 1024, 2048), reps=5, **kwargs):
+        """Time every candidate tile size; returns (best, {candidate: ms})."""
+        probe = Batch(plan, tile_elems=candidates[0], **kwargs)  # validates and holds the descriptor
+        cand = (ctypes.c_int * len(candidates))(*candidates)
+        ms = (ctypes.c_float * len(candidates))()
+        best = ctypes.c_int()
+        check(lib().q2x_batch_tune(plan.handle, ctypes.byref(probe._desc), cand, len(candidates), int(reps),
+                                   ctypes.byref(best), ms), plan.handle)
+        probe.close()
+        return int(best.value), {c: float(t) for c, t in zip(candidates, ms)}
+
+
+def autotuned_tile(plan: Plan, key: str, cache_path: str, **batch_kwargs) -> int:
+    """Tile size for a batch from the JSON autotune table at cache_path, keyed
+    by device name, precision, p_max and `key` (the caller's description of the
+    workload shape); tunes and records it when missing."""
+    import json
+    import os
+    dev = torch.cuda.get_device_name()
+    full = "%s|prec=%d|p=%d|%s" % (dev, plan.precision, plan.p_max, key)
+    table = {}
+    if os.path.exists(cache_path):
+        with open(cache_path) as f:
+            table = json.load(f)
+    if full in table:
+        return int(table[full]["tile_elems"])
+    best, times = Batch.tune(plan, **batch_kwargs)
+    table[full] = {"tile_elems": best, "ms": {str(k): v for k, v in times.items()}}
+    os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
+    tmp = cache_path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, cache_path)
+    return best

@@ -346,3 +346,51 @@ def random_triangles(n: int, seed: int, spread: float = 1.0, size: float = 0.05)
     v = np.concatenate([c + size * rng.standard_normal((3, n)) for _ in range(3)], axis=1)
     t = np.stack([np.arange(n), np.arange(n) + n, np.arange(n) + 2 * n]).astype(np.int32)
     return v, t
+
+
+def cfg_mixed_ball(n_fil=2000, n_steps=1000, step=1e-3, tri_level=9, n_tri=4_000_000, tet_spacing=0.0293,
+                   n_tet=1_000_000, max_per_leaf=2000, max_depth=12, p_lo=8, p_hi=20, seed=4):
+    """Mixed elements in the unit ball sharing one adaptive octree:
+    random-walk filament segments (density U[-1,1]), the first n_tri triangles
+    of the perturbed level-`tri_level` sphere scaled by 0.9 (constant density
+    U[-1,1]), and Kuhn tetrahedra of a jittered grid (density U[0,1]).  A box is
+    split while it holds more than max_per_leaf elements of any kind, up to
+    max_depth; per-leaf degree p_leaf ~ U{p_lo..p_hi}.
+    Returns dict(kinds={segment, triangle, tetra: dict(vxyz, idx, sigma,
+    leaf_off)}, leaf_c, leaf_rho, leaf_p, p)."""
+    rng = np.random.default_rng(seed)
+    kinds = {}
+    vs, es = filaments(n_fil, n_steps, step, seed=seed + 1)
+    kinds["segment"] = dict(vxyz=vs, idx=es, sigma=rng.uniform(-1, 1, es.shape[1]))
+    vt, tt = perturbed_sphere(tri_level, seed=seed + 2)
+    tt = np.ascontiguousarray(tt[:, :n_tri])
+    used, remap = np.unique(tt.reshape(-1), return_inverse=True)
+    tt = remap.reshape(3, -1).astype(np.int32)
+    vt = np.ascontiguousarray(0.9 * vt[:, used])
+    kinds["triangle"] = dict(vxyz=vt, idx=tt, sigma=rng.uniform(-1, 1, tt.shape[1]))
+    vq, tq = kuhn_tets(tet_spacing, seed=seed + 3, radius=1.0, max_tets=n_tet)
+    kinds["tetra"] = dict(vxyz=vq, idx=tq, sigma=rng.uniform(0, 1, tq.shape[1]))
+    names = ["segment", "triangle", "tetra"]
+    cents = [element_centres(kinds[k]["vxyz"], kinds[k]["idx"]) for k in names]
+    allc = np.concatenate(cents, axis=1)
+    order, leaf_of, leaf_c, leaf_h = adaptive_leaves(allc, -1.0, 2.0, max_per_leaf, max_depth)
+    n_leaves = leaf_c.shape[1]
+    leaf_all = np.empty(allc.shape[1], dtype=np.int64)
+    leaf_all[order] = leaf_of
+    base = 0
+    rho = np.zeros(n_leaves)
+    for k, c in zip(names, cents):
+        n = c.shape[1]
+        lk = leaf_all[base:base + n]
+        base += n
+        o = np.argsort(lk, kind="stable")
+        d = kinds[k]
+        d["idx"] = np.ascontiguousarray(d["idx"][:, o])
+        d["sigma"] = np.ascontiguousarray(d["sigma"][o])
+        d["leaf_off"] = csr_from_leaf_of(lk[o], n_leaves)
+        rho = np.maximum(rho, leaf_rho(d["vxyz"], d["idx"], d["leaf_off"], leaf_c))
+        d["vxyz"] = np.ascontiguousarray(d["vxyz"], dtype=np.float64)
+    rho = np.where(rho > 0, rho, 0.5 * np.sqrt(3.0) * leaf_h)
+    leaf_p = rng.integers(p_lo, p_hi + 1, size=n_leaves).astype(np.int32)
+    return dict(kinds=kinds, leaf_c=np.ascontiguousarray(leaf_c), leaf_rho=rho, leaf_p=leaf_p, p=int(p_hi),
+                name="mixed-ball")
