@@ -202,6 +202,28 @@ q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precision precisi
                                  const int32_t* leaf_p, double* coef_single, double* coef_double,
                                  int accumulate);
 
+/* Adjoint of q2x_triangles_single with constant density (the derivative of
+ * loss = sum_{leaves, c} grad_coef[L][c] * coef[L][c] with respect to the
+ * vertex coordinates and the densities).  Derived from Eq. (bas10) and the
+ * derivative rules of Eq. (bas5)-(bas8): d coef / d x_k is a Jacobian term
+ * plus J * int lambda_k grad R_n^{-m}, and each component of the latter is a
+ * double-layer moment (Eq. (rec15)) with a coordinate axis as the normal and
+ * the barycentric weight lambda_k of vertex k as a linear density.
+ *   grad_coef  double[n_leaves * (p_max+1)^2]  (device, read)
+ *   grad_vxyz  double[3 * n_vert] SoA (device): d loss / d vxyz is ADDED
+ *              (FP64 atomic accumulation over the elements sharing a vertex;
+ *              the summation order is not fixed)
+ *   grad_sigma double[n_elem] (device) or NULL: d loss / d sigma, overwritten
+ * Other arguments as in q2x_triangles_single.  In Q2X_FP32_MIXED the
+ * per-element sums run in FP32 (weights rho^{n+1} G, which flush to zero
+ * below the FP32 range), the accumulation into grad_vxyz in FP64. */
+q2x_status q2x_triangles_single_vjp(q2x_plan_t plan, int64_t n_elem, int64_t n_vert,
+                                    const double* vxyz, const int32_t* idx, const double* sigma,
+                                    int64_t n_leaves, const int64_t* leaf_off,
+                                    const double* leaf_c, const double* leaf_rho,
+                                    const int32_t* leaf_p, const double* grad_coef,
+                                    double* grad_vxyz, double* grad_sigma);
+
 /* ---- Ragged mixed batch in one persistent launch (CUDA graph) ----------
  * Several element kinds (segments, triangles, tetrahedra) share one leaf set;
  * every leaf has its own degree p_leaf <= p_max and its own element counts.

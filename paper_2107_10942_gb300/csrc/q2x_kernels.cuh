@@ -542,6 +542,8 @@ struct Frame {
     T XN, YN, ZN;              // the same for the unit normal (double layer)
     T s1, s2, s3;              // densities (vertex values for linear density)
     T seed;
+    T J;                       // Jacobian in the scaled frame
+    T eu[3], ev[3];            // edges x2 - x1, x3 - x1 (triangles; eu only for segments)
 };
 
 template <typename T, int KIND, int DENS>
@@ -700,6 +702,12 @@ __device__ __forceinline__ void load_frame(const double* __restrict__ vx, const 
     F.s2 = s2;
     F.s3 = s3;
     F.seed = seed;
+    F.J = J;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        F.eu[d] = edge[0][d];
+        F.ev[d] = edge[NV >= 3 ? 1 : 0][d];
+    }
 
 }
 

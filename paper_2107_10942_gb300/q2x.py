@@ -176,6 +176,24 @@ class Plan:
                                   int(bool(accumulate))), self._h)
         return cs, cd
 
+    def triangles_single_vjp(self, vxyz, idx, sigma, leaf_off, leaf_c, grad_coef, leaf_rho=None, leaf_p=None,
+                             grad_vxyz=None, grad_sigma=True):
+        """Adjoint of triangles(single layer, constant density): returns
+        (d loss/d vxyz, d loss/d sigma or None) for loss = sum(grad_coef * coef).
+        grad_vxyz, if given, is accumulated into (+=)."""
+        n_vert, n_elem = self._geom(vxyz, idx, 3)
+        _need(sigma, torch.float64, "sigma", (n_elem,))
+        n_leaves = self._leaf_args(n_elem, leaf_off, leaf_c, leaf_rho, leaf_p)
+        _need(grad_coef, torch.float64, "grad_coef", (n_leaves, n_coef(self.p_max)))
+        if grad_vxyz is None:
+            grad_vxyz = torch.zeros_like(vxyz)
+        _need(grad_vxyz, torch.float64, "grad_vxyz", tuple(vxyz.shape))
+        gs = torch.empty_like(sigma) if grad_sigma is True else grad_sigma
+        check(lib().q2x_triangles_single_vjp(self._h, n_elem, n_vert, _ptr(vxyz), _ptr(idx), _ptr(sigma), n_leaves,
+                                             _ptr(leaf_off), _ptr(leaf_c), _ptr(leaf_rho), _ptr(leaf_p),
+                                             _ptr(grad_coef), _ptr(grad_vxyz), _ptr(gs)), self._h)
+        return grad_vxyz, gs
+
     def leaf_reduce(self, elem, p, leaf_off, coef=None, accumulate=False):
         _need(elem, torch.float64, "elem")
         _need(leaf_off, torch.int64, "leaf_off")
@@ -305,3 +323,31 @@ def autotuned_tile(plan: Plan, key: str, cache_path: str, **batch_kwargs) -> int
         json.dump(table, f, indent=1, sort_keys=True)
     os.replace(tmp, cache_path)
     return best
+
+
+class TrianglesSingle(torch.autograd.Function):
+    """coef = Q2X single layer of constant-density triangles, differentiable in
+    the vertex coordinates and the densities (backward: the library's adjoint
+    kernel, q2x_triangles_single_vjp)."""
+
+    @staticmethod
+    def forward(ctx, vxyz, sigma, plan, idx, leaf_off, leaf_c, leaf_rho, leaf_p):
+        coef, _ = plan.triangles(vxyz.detach(), idx, sigma.detach(), leaf_off, leaf_c, leaf_rho, leaf_p,
+                                 density="const", single=True)
+        ctx.save_for_backward(vxyz, sigma)
+        ctx.plan = plan
+        ctx.rest = (idx, leaf_off, leaf_c, leaf_rho, leaf_p)
+        return coef
+
+    @staticmethod
+    def backward(ctx, grad_coef):
+        vxyz, sigma = ctx.saved_tensors
+        idx, leaf_off, leaf_c, leaf_rho, leaf_p = ctx.rest
+        gv, gs = ctx.plan.triangles_single_vjp(vxyz.detach(), idx, sigma.detach(), leaf_off, leaf_c,
+                                               grad_coef.contiguous(), leaf_rho, leaf_p)
+        return gv, gs, None, None, None, None, None, None
+
+
+def triangles_single(vxyz, sigma, plan, idx, leaf_off, leaf_c, leaf_rho=None, leaf_p=None):
+    """Differentiable single-layer Q2X of constant-density triangles."""
+    return TrianglesSingle.apply(vxyz, sigma, plan, idx, leaf_off, leaf_c, leaf_rho, leaf_p)

@@ -394,3 +394,22 @@ def cfg_mixed_ball(n_fil=2000, n_steps=1000, step=1e-3, tri_level=9, n_tri=4_000
     leaf_p = rng.integers(p_lo, p_hi + 1, size=n_leaves).astype(np.int32)
     return dict(kinds=kinds, leaf_c=np.ascontiguousarray(leaf_c), leaf_rho=rho, leaf_p=leaf_p, p=int(p_hi),
                 name="mixed-ball")
+
+
+def cfg_sphere_adjoint(level: int = 8, n_tri: int = 1_000_000, depth: int = 6, p: int = 12, seed_shape: int = 5,
+                       seed_sigma: int = 6, seed_g: int = 7):
+    """Perturbed level-`level` sphere truncated to its first n_tri triangles,
+    constant density U[-1,1], uniform octree of `depth`, and a seeded N(0,1)
+    adjoint G (one row of (p+1)^2 per leaf)."""
+    v, t = perturbed_sphere(level, seed_shape)
+    t = np.ascontiguousarray(t[:, :n_tri])
+    used, remap = np.unique(t.reshape(-1), return_inverse=True)
+    t = remap.reshape(3, -1).astype(np.int32)
+    v = np.ascontiguousarray(v[:, used])
+    rng = np.random.default_rng(seed_sigma)
+    sig = rng.uniform(-1.0, 1.0, size=t.shape[1])
+    order, leaf_of, leaf_c, _ = uniform_leaves(element_centres(v, t), -1.125, 2.25, depth)
+    prob = make_problem(v, t, sig, False, order, leaf_of, leaf_c, p)
+    prob.update(kind="triangle", density="const", layers=("single",), name="sphere-L%d-adjoint" % level)
+    prob["G"] = np.random.default_rng(seed_g).standard_normal((leaf_c.shape[1], (p + 1) ** 2))
+    return prob
