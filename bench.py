@@ -11,8 +11,10 @@ against the FP64 oracle on the CPU-baseline sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-For N > 1 launch with torch.distributed.run: every rank processes its own
-replica of the workload (weak scaling, no collective on the data path).
+For N > 1 launch with torch.distributed.run: the workload is replicated N
+times, the leaf list cut into N contiguous cost-balanced ranges and each rank
+runs its range (weak scaling; no collective on the data path, the step time is
+the max over ranks).
 """
 from __future__ import annotations
 
@@ -46,6 +48,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="sphere-L7-linear",
+                    choices=["sphere-L7-linear", "sphere-L9-const", "mixed-ball", "sphere-L8-adjoint"],
+                    help="workload; the default is the headline configuration, the others are the "
+                         "precision, ragged-batch and adjoint configurations")
     return ap.parse_args()
 
 
@@ -214,6 +220,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.config != "sphere-L7-linear":
+        import bench_configs
+        return bench_configs.run(args)
 
     import torch
     dist = None
@@ -233,7 +242,16 @@ def main():
     from paper_2107_10942_gb300.q2x import problem_to_device
     from paper_2107_10942_gb300.roofline import PEAK_FP32_FLOPS, PEAK_FP64_FLOPS, element_flops
 
-    prob = workload()
+    full = workload()
+    prob = full
+    if world > 1:
+        # weak scaling: `world` copies of the workload, leaves cut into
+        # contiguous cost-balanced ranges, one range per rank, no collective
+        from paper_2107_10942_gb300 import shard as S
+        rep = S.replicate_problem(full, world)
+        bounds = S.partition_leaves(S.leaf_costs(rep["leaf_off"], rep["leaf_p"], "triangle", "linear", 2), world)
+        prob = S.shard_problem(rep, bounds[rank], bounds[rank + 1])
+        del rep
     d = problem_to_device(prob, dev)
     n_elem = prob["idx"].shape[1]
     nc = (P + 1) ** 2
@@ -330,7 +348,12 @@ def main():
         dist.barrier()
 
     per_step = moments_per_step(prob)
-    value = world * per_step / (r64["ms"] * 1e-3)
+    total_moments = per_step
+    if dist:
+        t = torch.tensor([per_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_moments = float(t.item())
+    value = total_moments / (r64["ms"] * 1e-3)
     flops_elem = element_flops("triangle", "linear", ("single", "double"), P)
     achieved64 = flops_elem * n_elem / (r64["kernel_ms"] * 1e-3)
     achieved32 = flops_elem * n_elem / (r32["kernel_ms"] * 1e-3)
@@ -364,16 +387,16 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(prob), "precision": "fp64", "density": "linear",
-                   "layers": ["single", "double"], "p": P, "n_elem": n_elem,
-                   "moments_per_step": per_step, "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": {"workload": workload_name(full) + (" per rank" if world > 1 else ""), "precision": "fp64",
+                   "density": "linear", "layers": ["single", "double"], "p": P, "n_elem": n_elem,
+                   "moments_per_step": total_moments, "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "leaf-sharded dp%d (no collective)" % world if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved64 / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
                      "unit": "TFLOP/s", "frac": achieved64 / PEAK_FP64_FLOPS, "traffic": None,
                      "kernel": "q2x_elem_kernel<double,12,TRI,LINEAR>", "kernel_ms": r64["kernel_ms"],
                      "flops_per_launch": flops_elem * n_elem,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz (recipe FP64 1.25 TF)"},
-        "fp32_mixed": {"value": world * per_step / (r32["ms"] * 1e-3), "ms_per_step": r32["ms"],
+        "fp32_mixed": {"value": total_moments / (r32["ms"] * 1e-3), "ms_per_step": r32["ms"],
                        "speedup_vs_fp64": r64["ms"] / r32["ms"],
                        "roofline": {"bound": "alu", "achieved": achieved32 / 1e12, "peak": PEAK_FP32_FLOPS / 1e12,
                                     "unit": "TFLOP/s", "frac": achieved32 / PEAK_FP32_FLOPS,
@@ -381,7 +404,7 @@ def main():
                                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}},
         "errors_vs_oracle": errs or None,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * per_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": total_moments / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": r64["launches"],
         "clocks": clocks,

@@ -1,0 +1,226 @@
+"""Measurements of the non-headline workloads (run through `bench.py --config`):
+
+  sphere-L9-const   level-9 perturbed sphere, 5,242,880 triangles, constant
+                    density, depth-7 octree, p = 16: FP32-mixed vs FP64
+  mixed-ball        2M filament segments + 4M sphere triangles + 1M tetrahedra
+                    in the unit ball, adaptive octree (<= 2000 per leaf),
+                    p_leaf ~ U{8..20}: one CUDA-graph replay of the batch (FP32)
+  sphere-L8-adjoint 1M triangles of the perturbed level-8 sphere, depth 6,
+                    p = 12: FP32-mixed forward + adjoint (FP64 accumulation)
+
+Each prints one JSON line in the format of bench.py's (metric counted per
+output layer as elements x (p+1)^2, or sum over leaves of elements x
+(p_leaf+1)^2 for the ragged batch).  Errors against the FP64 oracle are
+measured on a few sampled leaves."""
+from __future__ import annotations
+
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+import workloads as W
+from bench import METRIC, UNIT, ClockSampler, L2_FLUSH_BYTES
+
+LINES = []
+
+
+def _norm_err(test, ref, rho, p, layer=0):
+    worst = 0.0
+    for L in range(ref.shape[0]):
+        s = np.zeros((p + 1) ** 2)
+        for n in range(p + 1):
+            for m in range(-n, n + 1):
+                f = math.sqrt(math.factorial(n + abs(m)) * math.factorial(n - abs(m)))
+                s[n * n + n + m] = f / rho[L] ** n
+        den = np.max(np.abs(ref[L] * s))
+        worst = max(worst, np.max(np.abs((test[L] - ref[L]) * s)) / den if den > 0 else 0.0)
+    return worst
+
+
+CLOCKS = {}
+
+
+def _time(fn, steps, warmup, flush, stream):
+    for _ in range(warmup):
+        flush.fill_(1.0)
+        fn()
+    torch.cuda.synchronize()
+    clk = ClockSampler()
+    clk.start()
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ms.append((a, b))
+    torch.cuda.synchronize()
+    CLOCKS.update(clk.stop())
+    return sum(x.elapsed_time(y) for x, y in ms) / steps
+
+
+def _emit(line):
+    line["clocks"] = dict(CLOCKS)
+    line["config"]["l2"] = "flushed between timed steps (256 MiB write)"
+    print(json.dumps(line), flush=True)
+
+
+def run_sphere_l9(args, dev):
+    import paper_2107_10942_gb300 as q
+    from paper_2107_10942_gb300.q2x import problem_to_device
+    from paper_2107_10942_gb300.roofline import PEAK_FP32_FLOPS, PEAK_FP64_FLOPS, element_flops
+    prob = W.cfg_sphere_const(level=9, depth=7, p=16)
+    d = problem_to_device({k: v for k, v in prob.items() if hasattr(v, "shape")}, dev)
+    p = 16
+    n_elem = prob["idx"].shape[1]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    res, outs = {}, {}
+    for prec in ("fp64", "fp32"):
+        plan = q.Plan(p, precision=prec)
+        coef = torch.empty((prob["leaf_c"].shape[1], (p + 1) ** 2), dtype=torch.float64, device=dev)
+        fn = lambda: plan.triangles(d["vxyz"], d["idx"], d["sigma"], d["leaf_off"], d["leaf_c"], d["leaf_rho"],
+                                    None, coef_single=coef)
+        ms = _time(fn, args.steps, args.warmup, flush, stream)
+        plan.set_kernel_timing(True)
+        plan.kernel_timing()
+        _time(fn, 3, 0, flush, stream)
+        kms, kn = plan.kernel_timing()
+        plan.sync()
+        res[prec] = (ms, kms / kn)
+        outs[prec] = coef.cpu().numpy()
+    flops = element_flops("triangle", "const", ("single",), p) * n_elem
+    import oracle as orc
+    rng = np.random.default_rng(3)
+    nl = prob["leaf_c"].shape[1]
+    pick = np.sort(rng.choice(nl, size=24, replace=False))
+    off = prob["leaf_off"]
+    ref = []
+    t0 = time.perf_counter()
+    ne = 0
+    for L in pick:
+        idx = np.ascontiguousarray(prob["idx"][:, off[L]:off[L + 1]])
+        ne += idx.shape[1]
+        ref.append(orc.moments("triangle", prob["vxyz"], idx, prob["sigma"][off[L]:off[L + 1]], p,
+                               leaf_off=np.array([0, idx.shape[1]]), leaf_c=prob["leaf_c"][:, L:L + 1])[0])
+    dt = time.perf_counter() - t0
+    ref = np.array(ref)
+    errs = {prec: _norm_err(outs[prec][pick], ref, prob["leaf_rho"][pick], p) for prec in outs}
+    per_step = n_elem * (p + 1) ** 2
+    _emit({"metric": METRIC, "value": per_step / (res["fp64"][0] * 1e-3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["fp64"][0], "higher_is_better": True,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "sphere-L9-const: %d triangles, depth 7 (%d leaves), p=16, single layer" % (n_elem, nl)},
+           "roofline": {"bound": "alu", "achieved": flops / (res["fp64"][1] * 1e-3) / 1e12,
+                        "peak": PEAK_FP64_FLOPS / 1e12, "unit": "TFLOP/s",
+                        "frac": flops / (res["fp64"][1] * 1e-3) / PEAK_FP64_FLOPS, "kernel_ms": res["fp64"][1]},
+           "fp32_mixed": {"value": per_step / (res["fp32"][0] * 1e-3), "ms_per_step": res["fp32"][0],
+                          "speedup_vs_fp64": res["fp64"][0] / res["fp32"][0],
+                          "roofline": {"bound": "alu", "achieved": flops / (res["fp32"][1] * 1e-3) / 1e12,
+                                       "peak": PEAK_FP32_FLOPS / 1e12, "unit": "TFLOP/s",
+                                       "frac": flops / (res["fp32"][1] * 1e-3) / PEAK_FP32_FLOPS,
+                                       "kernel_ms": res["fp32"][1]}},
+           "errors_vs_oracle": errs,
+           "cpu_baseline": {"value": ne * (p + 1) ** 2 / dt, "unit": UNIT, "kind": "oracle",
+                            "cores": orc.max_threads(), "sample": "%d triangles in 24 sampled leaves" % ne}})
+
+
+def run_mixed_ball(args, dev):
+    import paper_2107_10942_gb300 as q
+    m = W.cfg_mixed_ball()
+    kinds = {}
+    names = {"segment": "segments", "triangle": "triangles", "tetra": "tetra"}
+    for k, dd in m["kinds"].items():
+        kinds[names[k]] = {key: torch.from_numpy(v).to(dev) for key, v in dd.items()}
+    lc, lr, lp = (torch.from_numpy(m[k]).to(dev) for k in ("leaf_c", "leaf_rho", "leaf_p"))
+    plan = q.Plan(m["p"], precision="fp32")
+    tile = q.q2x.autotuned_tile(plan, "mixed-ball-%d" % m["leaf_c"].shape[1], "gpurun_out/autotune.json"
+                                if __import__("os").path.isdir("gpurun_out") else "/tmp/q2x_autotune.json",
+                                candidates=(128, 256, 512, 1024, 2048), reps=3, leaf_c=lc, leaf_rho=lr, leaf_p=lp,
+                                **kinds)
+    b = q.q2x.Batch(plan, lc, lr, lp, tile_elems=tile, **kinds)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ms = _time(b.run, args.steps, args.warmup, flush, stream)
+    got = b.coef.cpu().numpy()
+    plan.sync()
+    lpn = m["leaf_p"].astype(np.int64)
+    n_per_leaf = sum(np.diff(dd["leaf_off"]) for dd in m["kinds"].values())
+    per_step = int(np.sum(n_per_leaf * (lpn + 1) ** 2))
+    # oracle on 8 sampled leaves of 8..400 elements (bounded oracle time)
+    import oracle as orc
+    cand = np.nonzero((n_per_leaf >= 8) & (n_per_leaf <= 400))[0]
+    pick = np.sort(np.random.default_rng(4).choice(cand, size=min(8, len(cand)), replace=False))
+    t0 = time.perf_counter()
+    ref = np.zeros((len(pick), (m["p"] + 1) ** 2))
+    for i, L in enumerate(pick):
+        for k, dd in m["kinds"].items():
+            o = dd["leaf_off"]
+            if o[L + 1] > o[L]:
+                idx = np.ascontiguousarray(dd["idx"][:, o[L]:o[L + 1]])
+                ref[i] += orc.moments(k, dd["vxyz"], idx, dd["sigma"][o[L]:o[L + 1]], m["p"],
+                                      leaf_off=np.array([0, idx.shape[1]]), leaf_c=m["leaf_c"][:, L:L + 1],
+                                      leaf_p=m["leaf_p"][L:L + 1])[0]
+    dt = time.perf_counter() - t0
+    err = _norm_err(got[pick], ref, m["leaf_rho"][pick], m["p"])
+    info = b.info()
+    _emit({"metric": METRIC, "value": per_step / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32-mixed",
+           "data": "synthetic",
+           "config": {"workload": "mixed-ball: %d segments + %d triangles + %d tetrahedra, %d adaptive leaves, "
+                                  "p_leaf in 8..20" % tuple([m["kinds"][k]["idx"].shape[1] for k in
+                                                              ("segment", "triangle", "tetra")] +
+                                                             [m["leaf_c"].shape[1]]),
+                      "tiles": info["tiles"], "tile_elems": info["tile_elems"],
+                      "launch": "one CUDA-graph replay (counter reset, persistent kernel, combine)"},
+           "errors_vs_oracle": {"fp32": err, "sampled_leaves": len(pick)},
+           "cpu_baseline": {"value": float(np.sum(n_per_leaf[pick] * (lpn[pick] + 1) ** 2)) / dt, "unit": UNIT,
+                            "kind": "oracle", "cores": orc.max_threads(), "sample": "8 leaves"}})
+
+
+def run_adjoint(args, dev):
+    import paper_2107_10942_gb300 as q
+    from paper_2107_10942_gb300.q2x import problem_to_device
+    prob = W.cfg_sphere_adjoint(level=8, n_tri=1_000_000, depth=6, p=12)
+    d = problem_to_device({k: v for k, v in prob.items() if hasattr(v, "shape")}, dev)
+    p = 12
+    n_elem = prob["idx"].shape[1]
+    plan = q.Plan(p, precision="fp32")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    vx = d["vxyz"].clone().requires_grad_(True)
+    sg = d["sigma"].clone().requires_grad_(True)
+
+    def step():
+        coef = q.q2x.triangles_single(vx, sg, plan, d["idx"], d["leaf_off"], d["leaf_c"], d["leaf_rho"], None)
+        loss = torch.sum(coef * d["G"])
+        return torch.autograd.grad(loss, (vx, sg))
+
+    ms = _time(step, args.steps, args.warmup, flush, stream)
+    gv32, gs32 = (t.cpu().numpy() for t in step())
+    plan64 = q.Plan(p, precision="fp64")
+    gv64, gs64 = plan64.triangles_single_vjp(d["vxyz"], d["idx"], d["sigma"], d["leaf_off"], d["leaf_c"], d["G"],
+                                             d["leaf_rho"], None)
+    gv64, gs64 = gv64.cpu().numpy(), gs64.cpu().numpy()
+    rel_v = float(np.max(np.abs(gv32 - gv64)) / np.max(np.abs(gv64)))
+    rel_s = float(np.max(np.abs(gs32 - gs64)) / np.max(np.abs(gs64)))
+    per_step = n_elem * (p + 1) ** 2
+    _emit({"metric": METRIC + " (forward + adjoint)", "value": per_step / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "dtype": "f32-mixed forward, f32 per element + f64 accumulation backward", "data": "synthetic",
+           "config": {"workload": "sphere-L8-adjoint: %d triangles, depth 6, p=12, single layer, "
+                                  "loss = sum(G * coef), G ~ N(0,1)" % n_elem},
+           "errors_vs_fp64_adjoint": {"grad_vertices": rel_v, "grad_sigma": rel_s}})
+
+
+def run(args):
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    from paper_2107_10942_gb300 import build
+    build.build()
+    {"sphere-L9-const": run_sphere_l9, "mixed-ball": run_mixed_ball,
+     "sphere-L8-adjoint": run_adjoint}[args.config](args, dev)
