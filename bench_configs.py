@@ -1,5 +1,7 @@
 """Measurements of the non-headline workloads (run through `bench.py --config`):
 
+  icosphere-L3      1280 triangles of the level-3 icosphere, one expansion
+                    about the origin, p = 10, FP64 (latency-bound)
   sphere-L9-const   level-9 perturbed sphere, 5,242,880 triangles, constant
                     density, depth-7 octree, p = 16: FP32-mixed vs FP64
   mixed-ball        2M filament segments + 4M sphere triangles + 1M tetrahedra
@@ -217,10 +219,52 @@ def run_adjoint(args, dev):
            "errors_vs_fp64_adjoint": {"grad_vertices": rel_v, "grad_sigma": rel_s}})
 
 
+def run_icosphere_l3(args, dev):
+    import paper_2107_10942_gb300 as q
+    from paper_2107_10942_gb300.q2x import problem_to_device
+    import oracle as orc
+    prob = W.cfg_icosphere_l3(p=10)
+    d = to_dev(prob, dev)
+    p = 10
+    n_elem = prob["idx"].shape[1]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    plan = q.Plan(p, precision="fp64")
+    coef = torch.empty((1, (p + 1) ** 2), dtype=torch.float64, device=dev)
+    fn = lambda: plan.triangles(d["vxyz"], d["idx"], d["sigma"], d["leaf_off"], d["leaf_c"], d["leaf_rho"], None,
+                                coef_single=coef)
+    ms = _time(fn, args.steps, args.warmup, flush, stream)
+    got = coef.cpu().numpy()
+    plan.sync()
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        ref = orc.moments("triangle", prob["vxyz"], prob["idx"], prob["sigma"], p, leaf_off=prob["leaf_off"],
+                          leaf_c=prob["leaf_c"])
+        reps += 1
+        if time.perf_counter() - t0 > 2.0:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    per_step = n_elem * (p + 1) ** 2
+    _emit({"metric": METRIC, "value": per_step / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "icosphere-L3: %d triangles, one expansion about the origin, p=10, single layer, "
+                                  "constant density" % n_elem,
+                      "note": "latency-bound: one leaf, one warp range per 32 triangles"},
+           "errors_vs_oracle": {"fp64": _norm_err(got, ref, prob["leaf_rho"], p)},
+           "cpu_baseline": {"value": per_step / dt, "unit": UNIT, "kind": "oracle", "cores": orc.max_threads(),
+                            "sample": "the whole workload, %d repetitions" % reps}})
+
+
+def to_dev(prob, dev):
+    from paper_2107_10942_gb300.q2x import problem_to_device
+    return problem_to_device({k: v for k, v in prob.items() if hasattr(v, "shape")}, dev)
+
+
 def run(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     from paper_2107_10942_gb300 import build
     build.build()
-    {"sphere-L9-const": run_sphere_l9, "mixed-ball": run_mixed_ball,
+    {"icosphere-L3": run_icosphere_l3, "sphere-L9-const": run_sphere_l9, "mixed-ball": run_mixed_ball,
      "sphere-L8-adjoint": run_adjoint}[args.config](args, dev)

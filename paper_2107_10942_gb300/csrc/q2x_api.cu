@@ -266,8 +266,10 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
         if (occ <= 0) return fail(plan, Q2X_ERR_CUDA, "kernel does not fit on the device (smem %zu)", smem);
     }
     const int64_t resident_warps = (int64_t)occ * q2x::WARPS_PER_CTA * plan->num_sms;
+    // one range per resident warp (ranges need not be multiples of 32: rounds
+    // are formed per leaf inside the kernel), at least one full round each
     int64_t T = (n_elem + resident_warps - 1) / resident_warps;
-    T = std::max<int64_t>(32, (T + 31) / 32 * 32);
+    T = std::max<int64_t>(32, T);
     const int64_t n_ranges = (n_elem + T - 1) / T;
 
     // workspace: slots, then per-leaf scale (FP32 without leaf_rho)

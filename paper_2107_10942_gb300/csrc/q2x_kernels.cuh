@@ -314,17 +314,53 @@ __device__ __forceinline__ bool column_negative(int norm, int n, int m_signed)
     return neg;
 }
 
+// 1/k! (/4pi for COEFF) as an FP32 significand in [1, 2) and a power of two,
+// for the FP32 finish (compile-time table)
+struct FinishTab {
+    float mant[2][25];
+    int expo[2][25];
+};
+constexpr FinishTab make_finish_tab()
+{
+    FinishTab t{};
+    double f = 1.0;
+    for (int k = 0; k < 25; ++k) {
+        if (k > 0) f /= k;
+        for (int nm = 0; nm < 2; ++nm) {
+            double v = nm == 0 ? f * INV_4PI : f;
+            int e = 0;
+            while (v >= 2.0) {
+                v *= 0.5;
+                ++e;
+            }
+            while (v < 1.0) {
+                v *= 2.0;
+                --e;
+            }
+            float m = (float)v;
+            if (m >= 2.0f) {
+                m = 1.0f;
+                ++e;
+            }
+            t.mant[nm][k] = m;
+            t.expo[nm][k] = e;
+        }
+    }
+    return t;
+}
+static __constant__ FinishTab c_finish = make_finish_tab();
+
 // final coefficient of column (n, m) from a sum acc:
 // acc * sign / (n+d)! (/ 4pi for COEFF) * 2^shift
-// (FP32 sums are first turned exactly into FP64 and scaled there, so tiny
-// coefficients cannot underflow the FP32 range; this runs once per flushed
-// leaf column, not per moment)
+// FP32 sums: one FP32 multiply by the table significand (relative rounding
+// 2^-24), then the power of two is applied while re-biasing into FP64, so
+// tiny coefficients cannot underflow and no FP64 arithmetic is needed; this
+// runs once per flushed leaf column, not per moment.
 __device__ __forceinline__ double finish_value(float acc, int norm, int n, int m, int d, int shift)
 {
-    double cst = c_inv_fact_d[n + d];
-    if (norm == 0) cst *= INV_4PI;
-    if (column_negative(norm, n, m)) cst = -cst;
-    return f32_scaled_to_f64(acc, shift) * cst;
+    float v = acc * c_finish.mant[norm][n + d];
+    if (column_negative(norm, n, m)) v = -v;
+    return f32_scaled_to_f64(v, shift + c_finish.expo[norm][n + d]);
 }
 __device__ __forceinline__ double finish_value(double acc, int norm, int n, int m, int d, int shift)
 {
@@ -405,95 +441,108 @@ __device__ __forceinline__ void flush_value(const ElemArgs& a, const RangeCtx& r
     }
 }
 
-// Sum of col[r0..r1) with four interleaved partial sums (rows r = 4i + t go
-// to partial t), combined as (p0 + p1) + (p2 + p3): a fixed order, so results
-// are reproducible, and four independent dependency chains.
-__device__ __forceinline__ float sum_rows(const float* col, int r0, int r1)
-{
-    float p[4] = {0.f, 0.f, 0.f, 0.f};
-    int r = r0;
-    for (; r < r1 && (r & 3); ++r) p[r & 3] += col[r];
-    for (; r + 4 <= r1; r += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(col + r);
-        p[0] += v.x;
-        p[1] += v.y;
-        p[2] += v.z;
-        p[3] += v.w;
-    }
-    for (; r < r1; ++r) p[r & 3] += col[r];
-    return (p[0] + p[1]) + (p[2] + p[3]);
-}
-__device__ __forceinline__ double sum_rows(const double* col, int r0, int r1)
-{
-    double p[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 4
-    for (int r = r0; r < r1; ++r) p[r & 3] += col[r];
-    return (p[0] + p[1]) + (p[2] + p[3]);
-}
-
-// Sum of all 32 rows of a column: independent loads and a pairwise tree.
-__device__ __forceinline__ float sum_rows32(const float* col)
+// Sums of the eight groups of four rows of a staged column (rows 4g..4g+3 to
+// s[g], each as (r0 + r1) + (r2 + r3)); all loads independent.
+__device__ __forceinline__ void group_sums(const float* col, float (&s)[8])
 {
     float4 v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = *reinterpret_cast<const float4*>(col + 4 * i);
-    float s[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) s[i] = (v[i].x + v[i].y) + (v[i].z + v[i].w);
-    return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
-__device__ __forceinline__ double sum_rows32(const double* col)
+__device__ __forceinline__ void group_sums(const double* col, double (&s)[8])
 {
-    double s[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) s[i] = (col[4 * i] + col[4 * i + 1]) + (col[4 * i + 2] + col[4 * i + 3]);
+}
+
+// Sum of s[g] over groups g0 <= g < g1 as a fixed pairwise tree (groups
+// outside the interval contribute exact zeros).
+template <typename T>
+__device__ __forceinline__ T tree8(const T (&s)[8], int g0, int g1)
+{
+    T t[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) t[g] = (g >= g0 && g < g1) ? s[g] : T(0);
+    return ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+}
+
+// Sum of all 32 rows of a column (the single-leaf tiles of the batch kernel).
+template <typename T>
+__device__ __forceinline__ T sum_rows32(const T* col)
+{
+    T s[8];
+    group_sums(col, s);
     return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
 // Segmented column sums of one staged chunk: columns [c0, c0 + ncols) of each
-// wanted layer, rows 0..nrows-1.  bmask bit r: row r starts a new run (bit 0:
-// row 0 is not the open run's leaf).  The wanted layers' columns form one index
+// wanted layer.  Rows come in eight groups of four lanes; a leaf always starts
+// at a group boundary (the round assigns elements to lanes that way; padding
+// and idle lanes hold exact zeros), so a column is reduced by its eight group
+// sums: one pairwise tree when the whole round belongs to the open run
+// (gstart == 0), else the runs between the set bits of gstart (bit 4g: group
+// g starts a new leaf, whose id and info are rowleaf[4g], rowinfo[4g]) are
+// summed and flushed in order.  The wanted layers' columns form one index
 // space; lane j owns indices j, j+32, ...; the open run's sum lives in accb
-// between chunks and rounds.  A round that lies in one leaf and fills all 32
-// rows (the common case) takes the fast pairwise path.  All control flow is
-// warp-uniform.
+// between chunks and rounds.  Per-element expansions (no leaves): row r is
+// the complete expansion of element rowleaf[r], finished directly.  All
+// control flow is warp-uniform.
 template <typename T>
 __device__ __forceinline__ void reduce_chunk(const ElemArgs& a, const RangeCtx& rc, const T* tile,
                                              T* accb, const long long* rowleaf, const int* rowinfo,
-                                             long long open_leaf, int open_info, unsigned bmask,
-                                             int nrows, int c0, int ncols, bool want0, bool want1)
+                                             long long open_leaf, int open_info, unsigned gstart,
+                                             int nrows, int c0, int ncols, bool want0, bool want1,
+                                             bool per_elem)
 {
     constexpr int CH = KCfg<T>::CHUNK, LD = KCfg<T>::LD;
     const int lane = threadIdx.x & 31;
     const int nlay = (want0 ? 1 : 0) + (want1 ? 1 : 0);
     const int total = nlay * ncols;
-    const bool fast = (bmask == 0) && (nrows == 32);
+    if (per_elem) {
+#pragma unroll 1
+        for (int r = 0; r < nrows; ++r) {
+            const long long L = rowleaf[r];
+            const int info = rowinfo[r];
+#pragma unroll 1
+            for (int tc = lane; tc < total; tc += 32) {
+                const int second = (tc >= ncols) ? 1 : 0;
+                const int ly = want0 ? second : 1;
+                const int j = tc - second * ncols;
+                flush_value<T>(a, rc, ly, c0 + j, tile[(ly * CH + j) * LD + r], L, info);
+            }
+        }
+        return;
+    }
 #pragma unroll 1
     for (int tc = lane; tc < total; tc += 32) {
         const int second = (tc >= ncols) ? 1 : 0;
         const int ly = want0 ? second : 1;
         const int j = tc - second * ncols;
         const int c = c0 + j;
-        const T* col = tile + (ly * CH + j) * LD;
+        T s[8];
+        group_sums(tile + (ly * CH + j) * LD, s);
         T acc = accb[ly * a.np_max + c];
-        if (fast) {
-            acc += sum_rows32(col);
+        if (gstart == 0) {
+            acc += ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
         } else {
             long long L = open_leaf;
             int info = open_info;
-            unsigned mask = bmask;
-            int r = 0;
+            unsigned mask = gstart;
+            int g0 = 0;
             while (mask) {
-                const int rb = __ffs(mask) - 1;
-                acc += sum_rows(col, r, rb);
+                const int r = __ffs(mask) - 1;
+                const int g1 = r >> 2;
+                acc += tree8(s, g0, g1);
                 flush_value<T>(a, rc, ly, c, acc, L, info);
                 acc = T(0);
-                L = rowleaf[rb];
-                info = rowinfo[rb];
-                r = rb;
+                L = rowleaf[r];
+                info = rowinfo[r];
+                g0 = g1;
                 mask &= mask - 1;
             }
-            acc += sum_rows(col, r, nrows);
+            acc += tree8(s, g0, 8);
         }
         accb[ly * a.np_max + c] = acc;
     }
@@ -969,8 +1018,6 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
     constexpr int OUT = NL - 1;
     constexpr int NV = KIND + 2;
     constexpr int CH = KCfg<T>::CHUNK, LD = KCfg<T>::LD;
-    constexpr bool FP32 = sizeof(T) == 4;
-    constexpr bool LIN = (KIND == KIND_TRI && DENS == DENS_LINEAR);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -1036,14 +1083,63 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
     int open_info = leaf_info(rc.L_first);
     __syncwarp();
 
-    for (int64_t e0 = rc.e_lo; e0 < rc.e_hi; e0 += 32) {
-        const int64_t e = e0 + lane;
-        const bool active = e < rc.e_hi;
-        const int nrows = (int)min((int64_t)32, rc.e_hi - e0);
+    // Rounds of at most 32 elements.  The next 32 elements of the range are
+    // the candidates; candidate b that starts a new leaf is moved to the next
+    // multiple of four lanes (the lanes skipped are padding), candidates that
+    // no longer fit wait for the next round.  Per-element expansions take 32
+    // consecutive elements without padding.
+    int64_t e_cur = rc.e_lo;
+#pragma unroll 1
+    while (e_cur < rc.e_hi) {
+        const int64_t ec = e_cur + lane;
+        const bool cand = ec < rc.e_hi;
+        int64_t Lc = open_leaf;
+        if (cand) Lc = per_elem ? ec : leaf_search(a.leaf_off, open_leaf, L_last, ec);
+        const long long Lcprev = __shfl_up_sync(0xffffffffu, (long long)Lc, 1);
+        const bool cstart = cand && ((lane == 0) ? (Lc != open_leaf) : (Lc != Lcprev));
+        const unsigned B = __ballot_sync(0xffffffffu, cstart);
+        int my_off = 0;    // padding before this lane's candidate
+        int src_off = 0;   // padding before this lane's position
+        bool is_pad = false;
+        if (!per_elem) {
+            unsigned mk = B & ~1u;
+            int O = 0;
+            while (mk) {
+                const int bb = __ffs(mk) - 1;
+                mk &= mk - 1;
+                const int pp = bb + O;  // position of candidate bb before its own padding
+                if (pp >= 32) break;
+                const int pad = (-pp) & 3;
+                if (lane >= bb) my_off = O + pad;
+                if (lane >= pp) {
+                    is_pad = lane < pp + pad;
+                    src_off = O + pad;
+                }
+                O += pad;
+            }
+        }
+        const bool taken = cand && (lane + my_off) < 32;
+        const int n_taken = __popc(__ballot_sync(0xffffffffu, taken));
+        // this lane's element (position space)
+        const int ci = lane - src_off;
+        const bool active = !is_pad && ci < n_taken;
+        const int64_t e = e_cur + ci;
+        const long long Lsh = __shfl_sync(0xffffffffu, (long long)Lc, ci & 31);
+        const int64_t L = active ? (int64_t)Lsh : (int64_t)open_leaf;
+        // empty leaves between consecutive runs (overwrite mode)
+        if (!per_elem && !a.accumulate) {
+            unsigned mk = B & ((n_taken >= 32) ? 0xffffffffu : ((1u << n_taken) - 1u));
+            while (mk) {
+                const int bb = __ffs(mk) - 1;
+                mk &= mk - 1;
+                const long long cur = __shfl_sync(0xffffffffu, (long long)Lc, bb);
+                const long long prv = __shfl_sync(0xffffffffu, Lcprev, bb);
+                const long long prev = (bb == 0) ? open_leaf : prv;
+                if (cur > prev + 1) zero_leaves(prev + 1, cur);
+            }
+        }
 
-        // ---- this lane's leaf, centre, scale, degree
-        int64_t L = open_leaf;
-        if (active) L = per_elem ? e : leaf_search(a.leaf_off, open_leaf, L_last, e);
+        // ---- this lane's leaf centre, scale, degree
         unsigned errbits = 0;
         int pL = pw, sexp = 0, info = 0;
         double cx = 0.0, cy = 0.0, cz = 0.0;
@@ -1062,40 +1158,32 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
             sexp = info >> 1;
             if (!(finite_bits(cx) && finite_bits(cy) && finite_bits(cz))) errbits |= 2u;
         }
-        // run boundaries of this round (warp-uniform mask)
-        const long long Lprev = __shfl_up_sync(0xffffffffu, (long long)L, 1);
-        const bool starts = active && ((lane == 0) ? (L != open_leaf) : (L != Lprev));
-        const unsigned bmask = __ballot_sync(0xffffffffu, starts);
+        // group g (lanes 4g..4g+3) starts a new leaf: bit 4g
+        const unsigned gstart =
+            __ballot_sync(0xffffffffu, active && (lane & 3) == 0 && ((B >> (ci & 31)) & 1u));
+        const int last = 31 - __clz(__ballot_sync(0xffffffffu, active));
         rowleaf[lane] = (long long)L;
         rowinfo[lane] = info;
         __syncwarp();
-        if (!per_elem && !a.accumulate && bmask) {  // empty leaves between consecutive rows
-            unsigned mk = bmask;
-            while (mk) {
-                const int r = __ffs(mk) - 1;
-                const long long prev = (r == 0) ? open_leaf : rowleaf[r - 1];
-                if (rowleaf[r] > prev + 1) zero_leaves(prev + 1, rowleaf[r]);
-                mk &= mk - 1;
-            }
-        }
 
         Frame<T, NL> F;
         load_frame<T, KIND, DENS>(a.vx, a.vy, a.vz, a.idx, a.sigma, a.n_elem, a.n_vert, e, active, cx, cy, cz, sexp,
                                   errbits, pL, F);
         if (errbits) atomicOr(a.err, errbits);
         run_chain<T, P, KIND, DENS, OUTS>(F, pw, pL, tile, lane, [&](int c0, int ncols) {
-            reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, bmask, nrows, c0, ncols,
-                            want0, want1);
+            reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, gstart, n_taken, c0, ncols,
+                            want0, want1, per_elem);
         });
         // the run open at the end of this round
-        open_leaf = rowleaf[nrows - 1];
-        open_info = rowinfo[nrows - 1];
+        open_leaf = rowleaf[last];
+        open_info = rowinfo[last];
+        e_cur += n_taken;
         __syncwarp();
     }
 
     // ---- flush the run left open at the end of the range
 #pragma unroll 1
-    for (int ly = 0; ly < 2; ++ly) {
+    for (int ly = 0; ly < 2 && !per_elem; ++ly) {
         if ((ly == 0 && !want0) || (ly == 1 && !want1)) continue;
 #pragma unroll 1
         for (int c = lane; c < np; c += 32)

@@ -116,3 +116,24 @@ def test_fp32_adjoint_and_autograd(q2x, prob):
     gv, gs = gv.cpu().numpy(), gs.cpu().numpy()
     assert np.max(np.abs(gv - gv64)) <= 2e-5 * np.max(np.abs(gv64))
     assert np.max(np.abs(gs - gs64)) <= 2e-5 * np.max(np.abs(gs64))
+
+
+def test_high_degree_small_leaves(q2x, orc):
+    """p = 20 on depth-8 leaves (leaf scale 2^-7): FP64 adjoint against the
+    oracle's complex step, FP32-mixed against FP64."""
+    prob = W.cfg_sphere_adjoint(level=8, n_tri=1500, depth=8, p=20)
+    gv64, gs64 = gpu_grad(q2x, prob, "fp64")
+    gv32, gs32 = gpu_grad(q2x, prob, "fp32")
+    scale = np.max(np.abs(gv64))
+    assert np.max(np.abs(gv32 - gv64)) <= 2e-5 * scale
+    assert np.max(np.abs(gs32 - gs64)) <= 2e-5 * np.max(np.abs(gs64))
+    rng = np.random.default_rng(2)
+    vim = np.zeros_like(prob["vxyz"])
+    h = 1e-30
+    for v in rng.choice(np.unique(prob["idx"]), size=15, replace=False):
+        elems = np.where(np.any(prob["idx"] == v, axis=0))[0]
+        for d in range(3):
+            vim[d, v] = h
+            cs = oracle_loss_cs(orc, prob, prob["vxyz"], vim, elems).imag / h
+            vim[d, v] = 0.0
+            assert abs(gv64[d, v] - cs) <= 1e-10 * scale, (v, d, gv64[d, v], cs)
