@@ -87,7 +87,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& 
             Frame<T, C::NL> F;
             load_frame<T, KIND, DENS>(K.vx, K.vy, K.vz, K.idx, K.sigma, K.n_elem, K.n_vert, e, active, cx, cy,
                                       cz, sexp, errbits, pl, F);
-            run_chain<T, P, KIND, DENS, 1>(F, pL, pl, tile, lane, [&](int c0, int ncols) {
+            run_chain<T, P, KIND, DENS, 1>(F, pL, tile, lane, [&](int c0, int ncols) {
                 for (int j = lane; j < ncols; j += 32) accb[c0 + j] += sum_rows32(tile + j * LD);
             });
         }

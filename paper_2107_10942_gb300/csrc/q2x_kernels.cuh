@@ -249,13 +249,6 @@ __device__ __forceinline__ cf cf_fma(cf a, cf b, cf c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
     return r;
 }
-// (re, im) -> (im, re)
-__device__ __forceinline__ cf cf_swap(cf a)
-{
-    float re, im;
-    cf_parts(a, re, im);
-    return cf_make(im, re);
-}
 // (re, im) -> (-re, im), i.e. -conj
 __device__ __forceinline__ cf cf_negconj(cf a)
 {
@@ -278,7 +271,12 @@ __device__ __forceinline__ cf cf_zero()
 __device__ __forceinline__ cf cf_stencil(cf a, cf b, cf c, cf src, cf X2, cf YmY, cf nZ2)
 {
     const cf d = cf_sub(b, a);
-    const cf sw = cf_swap(cf_add(b, a));
+    // swap(a + b) with two scalar adds written straight into the swapped
+    // halves (no register moves)
+    float ar, ai, br, bi;
+    cf_parts(a, ar, ai);
+    cf_parts(b, br, bi);
+    const cf sw = cf_make(bi + ai, br + ar);
     cf t = cf_fma(nZ2, c, src);
     t = cf_fma(X2, d, t);
     return cf_fma(YmY, sw, t);
@@ -413,12 +411,15 @@ __device__ __forceinline__ int64_t leaf_lower(const int64_t* __restrict__ off, i
 // ------------------------------------------------------------ reduction
 
 // Run bookkeeping of one warp range.  A "run" is a maximal set of consecutive
-// rows of the same leaf.  info = (shift exponent << 1) | complete, where
-// complete means the leaf lies wholly in [e_lo, e_hi).
+// rows of the same leaf.  A leaf's info word = 128 * (scale exponent s) +
+// 2 * (p_leaf + 1) + complete, where complete means the leaf lies wholly in
+// [e_lo, e_hi) and p_leaf = -1 marks an invalid leaf degree (all zero).
+// Moments above p_leaf are computed like the others and dropped here, when
+// the leaf's sums are finished.
 struct RangeCtx {
     int64_t w, e_lo, e_hi, L_first;
-    int d_out[2];     // hat depth of each layer's output level
-    int shift_n0[2];  // shift = s * (n + shift_n0[layer])
+    int d_out0, d_out1;        // hat depth of each layer's output level
+    int shift_n00, shift_n01;  // shift = s * (n + shift_n0 of the layer)
 };
 
 template <typename T>
@@ -428,7 +429,10 @@ __device__ __forceinline__ void flush_value(const ElemArgs& a, const RangeCtx& r
     if (info & 1) {
         int n, m;
         col_nm(c, n, m);
-        const double v = finish_value(acc, a.norm, n, m, rc.d_out[ly], (info >> 1) * (n + rc.shift_n0[ly]));
+        double v = 0.0;
+        if (n < ((info >> 1) & 63))  // n <= p_leaf
+            v = finish_value(acc, a.norm, n, m, ly ? rc.d_out1 : rc.d_out0,
+                             (info >> 7) * (n + (ly ? rc.shift_n01 : rc.shift_n00)));
         double* dst = a.coef[ly] + (int64_t)L * a.np_max + c;
         if (a.accumulate)
             *dst += v;
@@ -766,7 +770,7 @@ __device__ __forceinline__ void load_frame(const double* __restrict__ vx, const 
 // in column order of the stage tile (layer 1 at tile + CHUNK*LD), and call
 // reduce(c0, ncols) whenever a chunk of columns [c0, c0 + ncols) is complete.
 template <typename T, int P, int KIND, int DENS, int OUTS, typename Reduce>
-__device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>& F, int pw, int pL, T* tile,
+__device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>& F, int pw, T* tile,
                                           int lane, Reduce&& reduce)
 {
     using C = Chain<KIND, DENS>;
@@ -806,7 +810,6 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
             for (int m = 0; m <= P; ++m) R[k][m] = cf_zero();
 #pragma unroll 1
         for (int n = 0; n <= pw; ++n) {
-            const bool keep = (n <= pL);
             float* trow0 = reinterpret_cast<float*>(tile) + (n * n - nb * nb + n) * LD + lane;
             float* trow1 = trow0 + CH * LD;
             const float c2f = (float)(n + 1) * (float)s2;
@@ -830,7 +833,6 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                                 cf dl = cf_stencil(a, b, c, cf_zero(), XN2, YNm, nZN2);
                                 float dr, di;
                                 cf_parts(dl, dr, di);
-                                if (!keep) dr = di = 0.f;
                                 if (st) {
                                     trow1[m * LD] = (m & 1) ? di : dr;
                                     if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
@@ -854,7 +856,6 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                         if (want0 && st) {
                             float vr, vi;
                             cf_parts(nw[OUT], vr, vi);
-                            if (!keep) vr = vi = 0.f;
                             trow0[m * LD] = (m & 1) ? vi : vr;
                             if (m > 0) trow0[-m * LD] = (m & 1) ? vr : vi;
                         }
@@ -880,7 +881,6 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
             for (int m = 0; m <= P; ++m) Rr[k][m] = Ri[k][m] = T(0);
 #pragma unroll 1
         for (int n = 0; n <= pw; ++n) {
-            const bool keep = (n <= pL);
             T* trow0 = tile + (n * n - nb * nb + n) * LD + lane;
             T* trow1 = trow0 + CH * LD;
             const T c2 = T(n + 1) * s2;
@@ -917,7 +917,6 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                                 di = fma(-ZN, ci, di);
                             }
                         }
-                        if (!keep) dr = di = T(0);
                         trow1[m * LD] = (m & 1) ? di : dr;
                         if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
                     }
@@ -964,7 +963,6 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                 }
                 if (want0) {
                     T vr = nr[OUT], vi = ni[OUT];
-                    if (!keep) vr = vi = T(0);
                     trow0[m * LD] = (m & 1) ? vi : vr;
                     if (m > 0) trow0[-m * LD] = (m & 1) ? vr : vi;
                 }
@@ -1041,10 +1039,10 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
     rc.w = w;
     rc.e_lo = w * a.T;
     rc.e_hi = min(rc.e_lo + a.T, a.n_elem);
-    rc.d_out[0] = C::D_OUT;
-    rc.d_out[1] = C::D_OUT - 1;
-    rc.shift_n0[0] = KIND + 1;
-    rc.shift_n0[1] = 1;
+    rc.d_out0 = C::D_OUT;
+    rc.d_out1 = C::D_OUT - 1;
+    rc.shift_n00 = KIND + 1;
+    rc.shift_n01 = 1;
 
     int64_t L_last;
     if (per_elem) {
@@ -1077,7 +1075,12 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
         bool complete = true;
         if (!per_elem) complete = __ldg(a.leaf_off + L) >= rc.e_lo && __ldg(a.leaf_off + L + 1) <= rc.e_hi;
         const int s = a.leaf_rho ? scale_exponent(__ldg(a.leaf_rho + L)) : 0;
-        return (s << 1) | (complete ? 1 : 0);
+        int pl = pw;
+        if (a.leaf_p) {
+            pl = __ldg(a.leaf_p + L);
+            if (pl < 0 || pl > pw) pl = -1;
+        }
+        return s * 128 + (pl + 1) * 2 + (complete ? 1 : 0);
     };
     long long open_leaf = rc.L_first;
     int open_info = leaf_info(rc.L_first);
@@ -1147,15 +1150,10 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
             cx = __ldg(a.leaf_c + L);
             cy = __ldg(a.leaf_c + a.n_leaves + L);
             cz = __ldg(a.leaf_c + 2 * a.n_leaves + L);
-            if (a.leaf_p) {
-                pL = __ldg(a.leaf_p + L);
-                if (pL < 0 || pL > pw) {
-                    errbits |= 4u;
-                    pL = -1;
-                }
-            }
             info = leaf_info(L);
-            sexp = info >> 1;
+            sexp = info >> 7;
+            pL = ((info >> 1) & 63) - 1;
+            if (pL < 0) errbits |= 4u;  // leaf degree out of range
             if (!(finite_bits(cx) && finite_bits(cy) && finite_bits(cz))) errbits |= 2u;
         }
         // group g (lanes 4g..4g+3) starts a new leaf: bit 4g
@@ -1170,7 +1168,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
         load_frame<T, KIND, DENS>(a.vx, a.vy, a.vz, a.idx, a.sigma, a.n_elem, a.n_vert, e, active, cx, cy, cz, sexp,
                                   errbits, pL, F);
         if (errbits) atomicOr(a.err, errbits);
-        run_chain<T, P, KIND, DENS, OUTS>(F, pw, pL, tile, lane, [&](int c0, int ncols) {
+        run_chain<T, P, KIND, DENS, OUTS>(F, pw, tile, lane, [&](int c0, int ncols) {
             reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, gstart, n_taken, c0, ncols,
                             want0, want1, per_elem);
         });
@@ -1210,6 +1208,11 @@ __global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d1)
     const int64_t wf = o0 / a.T;
     const int slot_first = (o0 == wf * a.T) ? 0 : 1;
     const int s = a.leaf_rho ? scale_exponent(__ldg(a.leaf_rho + L)) : 0;
+    int pl = a.p_max;
+    if (a.leaf_p) {
+        pl = __ldg(a.leaf_p + L);
+        if (pl < 0 || pl > a.p_max) pl = -1;
+    }
     const int np = a.np_max;
     const T* slots = reinterpret_cast<const T*>(a.slots);
     for (int ly = 0; ly < 2; ++ly) {
@@ -1231,7 +1234,7 @@ __global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d1)
             int n, m;
             col_nm(c, n, m);
             const int shift = s * (n + (ly == 0 ? dim : 1));
-            const double v = finish_value(sum, a.norm, n, m, ly == 0 ? d0 : d1, shift);
+            const double v = (n <= pl) ? finish_value(sum, a.norm, n, m, ly == 0 ? d0 : d1, shift) : 0.0;
             double* dst = a.coef[ly] + L * np + c;
             if (a.accumulate)
                 *dst += v;
