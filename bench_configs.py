@@ -170,6 +170,14 @@ def run_mixed_ball(args, dev):
     dt = time.perf_counter() - t0
     err = _norm_err(got[pick], ref, m["leaf_rho"][pick], m["p"])
     info = b.info()
+    from paper_2107_10942_gb300.roofline import PEAK_FP32_FLOPS, element_flops
+    kind_flops = {"segment": ("segment", "const"), "triangle": ("triangle", "const"), "tetra": ("tetra", "const")}
+    flops = 0.0
+    for k, dd in m["kinds"].items():
+        cnt = np.diff(dd["leaf_off"])
+        per_p = {pp: element_flops(kind_flops[k][0], kind_flops[k][1], ("single",), int(pp))
+                 for pp in np.unique(lpn)}
+        flops += float(sum(cnt[lpn == pp].sum() * f for pp, f in per_p.items()))
     _emit({"metric": METRIC, "value": per_step / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f32-mixed",
            "data": "synthetic",
@@ -179,6 +187,9 @@ def run_mixed_ball(args, dev):
                                                              [m["leaf_c"].shape[1]]),
                       "tiles": info["tiles"], "tile_elems": info["tile_elems"],
                       "launch": "one CUDA-graph replay (counter reset, persistent kernel, combine)"},
+           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP32_FLOPS / 1e12,
+                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP32_FLOPS,
+                        "note": "whole graph replay (reset + persistent kernel + combine) as the duration"},
            "errors_vs_oracle": {"fp32": err, "sampled_leaves": len(pick)},
            "cpu_baseline": {"value": float(np.sum(n_per_leaf[pick] * (lpn[pick] + 1) ** 2)) / dt, "unit": UNIT,
                             "kind": "oracle", "cores": orc.max_threads(), "sample": "8 leaves"}})
