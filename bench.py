@@ -38,6 +38,11 @@ METRIC = "Q2X element-moments/s (elems*(p+1)^2), FP32-mixed vs FP64 at stated re
 UNIT = "element-moments/s"
 LEVEL, DEPTH, P = 7, 5, 12
 L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64
+# element kernel on this workload, from the ncu capture summarised in the
+# profile named below (set to None whenever the kernel changes)
+TRAFFIC_FP64 = 9691392 + 39946496
+TRAFFIC_SOURCE = "ncu --set full, profiles/q2x_elem_kernel_sphere-L7-linear-p12.md (bytes per launch)"
 
 
 def parse():
@@ -393,7 +398,8 @@ def main():
                    "moments_per_step": total_moments, "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "leaf-sharded dp%d (no collective)" % world if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved64 / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
-                     "unit": "TFLOP/s", "frac": achieved64 / PEAK_FP64_FLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved64 / PEAK_FP64_FLOPS, "traffic": TRAFFIC_FP64,
+                     "traffic_source": TRAFFIC_SOURCE,
                      "kernel": "q2x_elem_kernel<double,12,TRI,LINEAR>", "kernel_ms": r64["kernel_ms"],
                      "flops_per_launch": flops_elem * n_elem,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz (recipe FP64 1.25 TF)"},
