@@ -99,11 +99,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& 
 #pragma unroll 1
     for (int c = lane; c < np; c += 32) {
         double v = 0.0;
-        if (c < npl) {
-            int n, m;
-            col_nm(c, n, m);
-            v = finish_value(accb[c], b.norm, n, m, C::D_OUT, sexp * (n + KIND + 1));
-        }
+        if (c < npl) v = finish_desc(accb[c], b.norm, col_desc(c), C::D_OUT, KIND + 1, sexp);
         out[c] = v;
     }
     __syncwarp();

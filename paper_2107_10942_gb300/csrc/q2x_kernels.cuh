@@ -55,6 +55,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "q2x.h"
+
 #include <type_traits>
 #include <utility>
 
@@ -348,6 +350,43 @@ constexpr FinishTab make_finish_tab()
 }
 static __constant__ FinishTab c_finish = make_finish_tab();
 
+// Per-column descriptor of the real packing k = n^2 + n + m (k < 441):
+// bits 0-4 the degree n, bit 5 / bit 6 the output sign (column_negative) for
+// COEFF / MOMENT.  A compile-time table read through the read-only cache, so
+// the flush of a leaf column needs no square root or sign logic.
+struct ColTab {
+    unsigned short v[(Q2X_P_MAX + 1) * (Q2X_P_MAX + 1)];
+};
+constexpr ColTab make_col_tab()
+{
+    ColTab t{};
+    for (int n = 0; n <= Q2X_P_MAX; ++n)
+        for (int m = -n; m <= n; ++m) {
+            const int am = m < 0 ? -m : m;
+            const int r = am & 3;
+            bool neg[2] = {false, false};
+            for (int nm = 0; nm < 2; ++nm) {
+                bool g = false;
+                if (m >= 0)
+                    g = r >= 2;
+                else if (nm == 0)
+                    g = !(r == 1 || r == 2);
+                else
+                    g = !(r == 0 || r == 3);
+                if (nm == 0 && ((n + am) & 1)) g = !g;
+                neg[nm] = g;
+            }
+            t.v[n * n + n + m] = (unsigned short)(n | (neg[0] ? 32 : 0) | (neg[1] ? 64 : 0));
+        }
+    return t;
+}
+static __device__ const ColTab g_coltab = make_col_tab();
+
+__device__ __forceinline__ int col_desc(int c)
+{
+    return (int)__ldg(&g_coltab.v[c]);
+}
+
 // final coefficient of column (n, m) from a sum acc:
 // acc * sign / (n+d)! (/ 4pi for COEFF) * 2^shift
 // FP32 sums: one FP32 multiply by the table significand (relative rounding
@@ -366,6 +405,23 @@ __device__ __forceinline__ double finish_value(double acc, int norm, int n, int 
     if (norm == 0) cst *= INV_4PI;
     if (column_negative(norm, n, m)) cst = -cst;
     return acc * cst * pow2d(shift);
+}
+
+// the same from a column descriptor (col_desc): n and the sign from the table
+__device__ __forceinline__ double finish_desc(float acc, int norm, int desc, int d, int shift_n0, int s)
+{
+    const int n = desc & 31;
+    float v = acc * c_finish.mant[norm][n + d];
+    if ((desc >> (5 + norm)) & 1) v = -v;
+    return f32_scaled_to_f64(v, s * (n + shift_n0) + c_finish.expo[norm][n + d]);
+}
+__device__ __forceinline__ double finish_desc(double acc, int norm, int desc, int d, int shift_n0, int s)
+{
+    const int n = desc & 31;
+    double cst = c_inv_fact_d[n + d];
+    if (norm == 0) cst *= INV_4PI;
+    if ((desc >> (5 + norm)) & 1) cst = -cst;
+    return acc * cst * pow2d(s * (n + shift_n0));
 }
 
 // compile-time loop: f(std::integral_constant<int, I>) for I in [B, E)
@@ -427,12 +483,11 @@ __device__ __forceinline__ void flush_value(const ElemArgs& a, const RangeCtx& r
                                             T acc, long long L, int info)
 {
     if (info & 1) {
-        int n, m;
-        col_nm(c, n, m);
+        const int desc = col_desc(c);
         double v = 0.0;
-        if (n < ((info >> 1) & 63))  // n <= p_leaf
-            v = finish_value(acc, a.norm, n, m, ly ? rc.d_out1 : rc.d_out0,
-                             (info >> 7) * (n + (ly ? rc.shift_n01 : rc.shift_n00)));
+        if ((desc & 31) < ((info >> 1) & 63))  // n <= p_leaf
+            v = finish_desc(acc, a.norm, desc, ly ? rc.d_out1 : rc.d_out0, ly ? rc.shift_n01 : rc.shift_n00,
+                            info >> 7);
         double* dst = a.coef[ly] + (int64_t)L * a.np_max + c;
         if (a.accumulate)
             *dst += v;
@@ -1231,10 +1286,10 @@ __global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d1)
                 sum = t;
             }
             sum += comp;
-            int n, m;
-            col_nm(c, n, m);
-            const int shift = s * (n + (ly == 0 ? dim : 1));
-            const double v = (n <= pl) ? finish_value(sum, a.norm, n, m, ly == 0 ? d0 : d1, shift) : 0.0;
+            const int desc = col_desc(c);
+            const double v = ((desc & 31) <= pl)
+                                 ? finish_desc(sum, a.norm, desc, ly == 0 ? d0 : d1, ly == 0 ? dim : 1, s)
+                                 : 0.0;
             double* dst = a.coef[ly] + L * np + c;
             if (a.accumulate)
                 *dst += v;
