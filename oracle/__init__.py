@@ -177,3 +177,67 @@ def farfield(coef, c, pts, p) -> np.ndarray:
     if lib().oracle_farfield(p, _ptr(coef), _ptr(c), pts.shape[0], _ptr(pts), _ptr(out), _ptr(oim)):
         raise ValueError("bad p")
     return out, oim
+
+
+# ---------------------------------------------------------------- translation
+
+def unpack_complex(coef, p):
+    """Packed real rows (..., (p+1)^2) -> complex F_n^m for every m in -n..n
+    (same index k = n*n+n+m), using F_n^{-m} = (-1)^m conj(F_n^m), Eq. (bas2.1)."""
+    coef = np.asarray(coef, dtype=np.float64)
+    F = np.zeros(coef.shape, dtype=np.complex128)
+    for n in range(p + 1):
+        k0 = n * n + n
+        F[..., k0] = coef[..., k0]
+        for m in range(1, n + 1):
+            v = coef[..., k0 + m] + 1j * coef[..., k0 - m]
+            F[..., k0 + m] = v
+            F[..., k0 - m] = (-1) ** m * np.conj(v)
+    return F
+
+
+def pack_complex(F, p):
+    """Complex F_n^m (all m) -> packed real rows (Re at m >= 0, Im F^{|m|} at m < 0)."""
+    out = np.zeros(F.shape, dtype=np.float64)
+    for n in range(p + 1):
+        k0 = n * n + n
+        out[..., k0] = F[..., k0].real
+        for m in range(1, n + 1):
+            out[..., k0 + m] = F[..., k0 + m].real
+            out[..., k0 - m] = F[..., k0 + m].imag
+    return out
+
+
+def translate(coef, src_c, dst_c, p, norm=NORM_COEFF):
+    """Expansion coefficients about dst_c from those about src_c, one row per
+    expansion (coef (N, (p+1)^2) packed, src_c and dst_c (3, N)), exact for
+    every degree n <= p.
+
+    With x = y - src_c and t = src_c - dst_c, the Taylor series of R_n^m in
+    (xi, eta, z) and the derivative rules of Eq. (bas5) give the finite sum
+        R_n^m(x + t) = sum_{k=0..n} sum_{l=-k..k} R_k^l(t) R_{n-k}^{m-l}(x),
+    so, term by term in Eq. (bas4):
+        MOMENT: M_n^m(dst) = sum_{k,l} R_k^l(t) M_{n-k}^{m-l}(src)
+        COEFF : F_n^m(dst) = sum_{k,l} (-1)^k R_k^l(t) F_{n-k}^{m+l}(src)
+    (the double-layer coefficients translate the same way: n.grad commutes
+    with the shift).  Plain loops over (n, m, k, l), vectorised over rows."""
+    coef = np.atleast_2d(np.asarray(coef, dtype=np.float64))
+    src_c = np.asarray(src_c, dtype=np.float64).reshape(3, -1)
+    dst_c = np.asarray(dst_c, dtype=np.float64).reshape(3, -1)
+    N = coef.shape[0]
+    F = unpack_complex(coef, p)
+    R = np.stack([rnm(src_c[:, i] - dst_c[:, i], p) for i in range(N)])  # (N, (p+1)^2)
+    G = np.zeros_like(F)
+    for n in range(p + 1):
+        for m in range(-n, n + 1):
+            acc = np.zeros(N, dtype=np.complex128)
+            for k in range(n + 1):
+                nn = n - k
+                sk = (-1) ** k if norm == NORM_COEFF else 1
+                for l in range(-k, k + 1):
+                    mm = m + l if norm == NORM_COEFF else m - l
+                    if abs(mm) > nn:
+                        continue
+                    acc += sk * R[:, k * k + k + l] * F[:, nn * nn + nn + mm]
+            G[:, n * n + n + m] = acc
+    return pack_complex(G, p)
