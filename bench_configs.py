@@ -267,6 +267,57 @@ def run_icosphere_l3(args, dev):
                             "sample": "the whole workload, %d repetitions" % reps}})
 
 
+def translate_macs(p):
+    """complex multiply-adds of one translation of degree p (COEFF formula)"""
+    t = 0
+    for n in range(p + 1):
+        for m in range(n + 1):
+            for k in range(n + 1):
+                nn = n - k
+                t += max(0, min(k, nn - m) - max(-k, -nn - m) + 1)
+    return t
+
+
+def run_upward(args, dev):
+    import paper_2107_10942_gb300 as q
+    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS
+    from paper_2107_10942_gb300.upward import Upward
+    import oracle as orc
+    p, depth = 12, 5
+    prob = W.cfg_sphere_linear(level=7, depth=depth, p=p)
+    d = to_dev(prob, dev)
+    plan = q.Plan(p, precision="fp64")
+    leaf, _ = plan.triangles(d["vxyz"], d["idx"], d["sigma"], d["leaf_off"], d["leaf_c"], d["leaf_rho"], None,
+                             density="linear")
+    up = Upward(plan, d["leaf_c"], -1.125, 2.25, depth)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ms = _time(lambda: up.run(leaf), args.steps, args.warmup, flush, stream)
+    outs = up.run(leaf)
+    root = outs[-1].cpu().numpy()
+    plan.sync()
+    n_tr = sum(int(lv["dst_off"][-1]) for lv in up.levels)
+    flops = 8.0 * translate_macs(p) * n_tr
+    # the root against quadrature of the whole sphere about the cube centre
+    t0 = time.perf_counter()
+    ref = orc.moments("triangle", prob["vxyz"], prob["idx"], prob["sigma"], p,
+                      leaf_off=np.array([0, prob["idx"].shape[1]]), leaf_c=np.zeros((3, 1)), density=1)
+    dt = time.perf_counter() - t0
+    rho = np.max(np.linalg.norm(prob["vxyz"], axis=0))
+    err = _norm_err(root, ref, np.array([rho]), p)
+    _emit({"metric": "M2M translations/s (upward pass of the leaf coefficients)", "value": n_tr / (ms * 1e-3),
+           "unit": "translations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "upward pass of the level-7 sphere's depth-5 leaves (%d leaves, %d translations, "
+                                  "5 levels), p=12, FP64" % (prob["leaf_c"].shape[1], n_tr)},
+           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
+                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP64_FLOPS,
+                        "flops_per_translation": 8 * translate_macs(p)},
+           "errors_vs_oracle": {"root_vs_quadrature": err},
+           "cpu_baseline": {"value": None, "note": "oracle quadrature of the root expansion over all %d triangles: "
+                            "%.2f s" % (prob["idx"].shape[1], dt), "kind": "oracle", "cores": orc.max_threads()}})
+
+
 def to_dev(prob, dev):
     from paper_2107_10942_gb300.q2x import problem_to_device
     return problem_to_device({k: v for k, v in prob.items() if hasattr(v, "shape")}, dev)
@@ -277,5 +328,5 @@ def run(args):
     torch.cuda.set_device(dev)
     from paper_2107_10942_gb300 import build
     build.build()
-    {"icosphere-L3": run_icosphere_l3, "sphere-L9-const": run_sphere_l9, "mixed-ball": run_mixed_ball,
+    {"icosphere-L3": run_icosphere_l3, "sphere-L9-const": run_sphere_l9, "upward": run_upward, "mixed-ball": run_mixed_ball,
      "sphere-L8-adjoint": run_adjoint}[args.config](args, dev)

@@ -276,6 +276,31 @@ q2x_status q2x_batch_info(q2x_batch_t batch, int64_t* n_tiles, int64_t* n_slots,
 q2x_status q2x_batch_tune(q2x_plan_t plan, const q2x_batch_desc* desc, const int* candidates,
                           int n_candidates, int reps, int* best, float* ms);
 
+/* Translation of expansions to new centres: the multipole-to-multipole step
+ * that consumes the leaf coefficients (the paper stops at Eq. (st4); the
+ * formula follows from the derivative rules of Eq. (bas5), whose Taylor
+ * series gives R_n^m(x + t) = sum_{k<=n} sum_{|l|<=k} R_k^l(t) R_{n-k}^{m-l}(x)):
+ *   COEFF : F_n^m(dst) = sum_{k,l} (-1)^k R_k^l(t) F_{n-k}^{m+l}(src)
+ *   MOMENT: M_n^m(dst) = sum_{k,l} R_k^l(t) M_{n-k}^{m-l}(src)
+ * with t = src centre - dst centre; exact for every degree n <= p (no
+ * truncation), single and double layer alike.  The plan's norm selects the
+ * formula.
+ *   p          degree, 0..the plan's p_max; every row has (p+1)^2 entries
+ *   src_coef   double[n_src * (p+1)^2], packed like coef above (device)
+ *   src_c      double[3 * n_src] SoA source centres (device)
+ *   dst_off    int64[n_dst + 1] CSR: destination d receives the sources
+ *              dst_off[d] .. dst_off[d+1]-1 (device); a bad range sets the
+ *              device error word (bit 8) and that destination gets zeros
+ *   dst_c      double[3 * n_dst] SoA destination centres (device)
+ *   dst_coef   double[n_dst * (p+1)^2] (device): overwritten, or added to
+ *              with accumulate = 1
+ * Sums run in source order (deterministic).  FP64 arithmetic in both
+ * precisions of the plan.  One upward pass of an octree is one call per
+ * level (children -> parents). */
+q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const double* src_coef,
+                         const double* src_c, int64_t n_dst, const int64_t* dst_off,
+                         const double* dst_c, double* dst_coef, int accumulate);
+
 /* Segmented sum of per-element coefficient rows into leaves (Eq. (st4)):
  * coef[L] (+)= sum_{e in leaf L} elem[e], elem double[n_elem * (p+1)^2],
  * coef double[n_leaves * (p+1)^2], leaf_off as above (required).  FP64,

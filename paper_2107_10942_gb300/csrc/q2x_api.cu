@@ -356,6 +356,11 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
 
 // ===================================================================== ABI
 
+q2x_status q2x_plan_workspace(q2x_plan_t plan, size_t bytes)
+{
+    return ensure_ws(plan, bytes);
+}
+
 extern "C" {
 
 q2x_status q2x_plan(q2x_plan_t* out, int p_max, q2x_norm norm, q2x_precision precision,

@@ -31,3 +31,6 @@ struct q2x_plan_s {
 // status helpers shared by the library's translation units
 q2x_status q2x_fail(q2x_plan_t plan, q2x_status st, const char* fmt, ...);
 q2x_status q2x_cuda_fail(q2x_plan_t plan, cudaError_t e, const char* what);
+// grow the plan's device workspace to at least `bytes` (synchronises the
+// plan's stream when it has to reallocate)
+q2x_status q2x_plan_workspace(q2x_plan_t plan, size_t bytes);

@@ -52,20 +52,8 @@ extern "C" q2x_status q2x_triangles_single_vjp(q2x_plan_t plan, int64_t n_elem, 
     while (bins[bin] < plan->p_max) ++bin;
     // workspace: the per-leaf weights (grows the plan's buffer if needed)
     const size_t bytes = (prec ? sizeof(float) : sizeof(double)) * (size_t)n_leaves * np;
-    if (bytes > plan->ws_bytes) {
-        if (plan->ws) {
-            cudaStreamSynchronize(plan->stream);
-            cudaFree(plan->ws);
-            plan->ws = nullptr;
-            plan->ws_bytes = 0;
-        }
-        const size_t alloc = (bytes + (1 << 20) - 1) / (1 << 20) * (1 << 20);
-        if (cudaMalloc(&plan->ws, alloc) != cudaSuccess) {
-            cudaGetLastError();
-            return q2x_fail(plan, Q2X_ERR_OOM, "vjp: workspace allocation of %zu bytes failed", alloc);
-        }
-        plan->ws_bytes = alloc;
-    }
+    q2x_status st = q2x_plan_workspace(plan, bytes);
+    if (st != Q2X_OK) return st;
     const int64_t nw = n_leaves * np;
     const unsigned wgrid = (unsigned)((nw + 255) / 256);
     if (prec)

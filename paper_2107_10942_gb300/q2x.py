@@ -211,6 +211,30 @@ class Plan:
         return coef
 
 
+    def translate(self, src_coef, src_c, dst_off, dst_c, dst_coef=None, accumulate=False, p=None):
+        """Expansions about src_c (rows of src_coef) translated to the
+        destination centres dst_c and summed per destination over the CSR
+        ranges dst_off (q2x_translate).  Returns dst_coef (n_dst, (p+1)^2)."""
+        p = self.p_max if p is None else int(p)
+        nc = n_coef(p)
+        _need(src_coef, torch.float64, "src_coef")
+        if src_coef.dim() != 2 or src_coef.shape[1] != nc:
+            raise ValueError("src_coef must be (n_src, (p+1)^2)")
+        n_src = src_coef.shape[0]
+        _need(src_c, torch.float64, "src_c", (3, n_src))
+        _need(dst_off, torch.int64, "dst_off")
+        n_dst = dst_off.shape[0] - 1
+        _need(dst_c, torch.float64, "dst_c", (3, n_dst))
+        if dst_coef is None:
+            if accumulate:
+                raise ValueError("accumulate=True needs an output tensor")
+            dst_coef = torch.empty((n_dst, nc), dtype=torch.float64, device=src_coef.device)
+        _need(dst_coef, torch.float64, "dst_coef", (n_dst, nc))
+        check(lib().q2x_translate(self._h, p, n_src, _ptr(src_coef), _ptr(src_c), n_dst, _ptr(dst_off),
+                                  _ptr(dst_c), _ptr(dst_coef), int(bool(accumulate))), self._h)
+        return dst_coef
+
+
 def problem_to_device(prob: dict, device="cuda") -> dict:
     """Copy a workloads-style problem dict (numpy arrays) to device tensors."""
     out = {}

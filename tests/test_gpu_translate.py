@@ -1,0 +1,125 @@
+"""GPU tests of q2x_translate (the M2M step fed by the Q2X leaf coefficients)
+and of the octree upward pass built on it: against the oracle's translation
+on random expansions (ragged source counts, every degree bin, both norms),
+and, end to end, the root and mid-level coefficients of an upward pass
+against the oracle's quadrature about those centres."""
+import numpy as np
+import pytest
+
+import workloads as W
+from _helpers import norm_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q2x():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_10942_gb300 import build
+    build.build()
+    import paper_2107_10942_gb300 as q
+    return q
+
+
+def oracle_translate_sum(orc, coef, src_c, off, dst_c, p, norm):
+    out = np.zeros((len(off) - 1, (p + 1) ** 2))
+    for d in range(len(off) - 1):
+        s0, s1 = off[d], off[d + 1]
+        if s1 > s0:
+            moved = orc.translate(coef[s0:s1], src_c[:, s0:s1], np.repeat(dst_c[:, d:d + 1], s1 - s0, axis=1), p,
+                                  norm=norm)
+            for r in moved:  # in source order, like the kernel
+                out[d] += r
+    return out
+
+
+@pytest.mark.parametrize("p", [0, 1, 5, 12, 20])
+@pytest.mark.parametrize("norm", ["coeff", "moment"])
+def test_translate_matches_oracle(q2x, orc, p, norm):
+    rng = np.random.default_rng(p + 7)
+    counts = np.array([0, 1, 8, 3, 0, 9, 2, 8, 1, 5, 4, 8, 0, 7, 6, 1, 2, 33])
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    n_src, n_dst = int(off[-1]), len(counts)
+    dst_c = rng.uniform(-1, 1, (3, n_dst))
+    src_c = np.repeat(dst_c, counts, axis=1) + rng.uniform(-0.2, 0.2, (3, n_src))
+    coef = rng.standard_normal((n_src, (p + 1) ** 2))
+    nrm = 0 if norm == "coeff" else 1
+    ref = oracle_translate_sum(orc, coef, src_c, off, dst_c, p, nrm)
+    plan = q2x.Plan(p, norm=norm, precision="fp64")
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    got = plan.translate(T(coef), T(src_c), T(off), T(dst_c)).cpu().numpy()
+    plan.sync()
+    scale = np.max(np.abs(ref), axis=1, keepdims=True)
+    scale[scale == 0] = 1.0
+    assert np.max(np.abs(got - ref) / scale) <= 1e-13
+    assert np.all(got[counts == 0] == 0)
+    # accumulate adds in place
+    base = rng.standard_normal(ref.shape)
+    acc = T(base.copy())
+    plan.translate(T(coef), T(src_c), T(off), T(dst_c), dst_coef=acc, accumulate=True)
+    plan.sync()
+    assert np.max(np.abs(acc.cpu().numpy() - (base + got))) <= 1e-13 * np.max(np.abs(base + got))
+
+
+def test_translate_bad_offsets_flagged(q2x):
+    plan = q2x.Plan(4, precision="fp64")
+    coef = torch.ones((3, 25), dtype=torch.float64, device="cuda")
+    c = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
+    off = torch.tensor([0, 2, 9], dtype=torch.int64, device="cuda")  # beyond n_src
+    dc = torch.zeros((3, 2), dtype=torch.float64, device="cuda")
+    out = plan.translate(coef, c, off, dc)
+    with pytest.raises(q2x.Q2XError):
+        plan.sync()
+    assert torch.all(out[1] == 0)
+    coef5 = torch.ones((3, 36), dtype=torch.float64, device="cuda")
+    with pytest.raises(q2x.Q2XError) as ei:
+        plan.translate(coef5, c, off, dc, p=5)  # above the plan's p_max
+    assert ei.value.status == 2
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_upward_pass_against_quadrature(q2x, orc, prec):
+    """Level-4 perturbed sphere, linear density, depth-3 leaves, p = 10: Q2X at
+    the leaves then the upward pass; the root (about the cube centre) and two
+    level-1 boxes are checked against the oracle's quadrature about those
+    centres over all the triangles they contain."""
+    from paper_2107_10942_gb300.q2x import problem_to_device
+    from paper_2107_10942_gb300.upward import Upward
+    p, depth, lo, size = 10, 3, -1.125, 2.25
+    prob = W.cfg_sphere_linear(level=4, depth=depth, p=p)
+    d = problem_to_device({k: v for k, v in prob.items() if hasattr(v, "shape")})
+    plan = q2x.Plan(p, precision=prec)
+    leaf, _ = plan.triangles(d["vxyz"], d["idx"], d["sigma"], d["leaf_off"], d["leaf_c"], d["leaf_rho"], None,
+                             density="linear")
+    plan64 = q2x.Plan(p, precision="fp64")
+    up = Upward(plan64, d["leaf_c"], lo, size, depth)
+    levels = up.run(leaf)
+    plan.sync()
+    plan64.sync()
+    root = levels[-1].cpu().numpy()
+    assert root.shape[0] == 1 and np.allclose(up.levels[-1]["c"][:, 0], 0.0)
+    all_idx = prob["idx"]
+    ref = orc.moments("triangle", prob["vxyz"], all_idx, prob["sigma"], p, leaf_off=np.array([0, all_idx.shape[1]]),
+                      leaf_c=np.zeros((3, 1)), density=1)
+    rho = np.max(np.linalg.norm(prob["vxyz"], axis=0))
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert norm_err(root, ref, p, [rho], 0) <= tol
+    # level 1 (8 boxes of half size): boxes 0 and 5 against quadrature over their leaves
+    lvl1 = levels[-2].cpu().numpy()
+    lv = up.levels
+    # leaves of each level-1 box via the CSR chain leaves -> depth-1 -> ... -> level 1
+    owner = np.arange(prob["leaf_c"].shape[1])
+    for lvd in lv[:-1]:
+        parent_of = np.repeat(np.arange(len(lvd["dst_off"]) - 1), np.diff(lvd["dst_off"]))
+        owner = parent_of[owner]
+    leaf_owner = np.repeat(owner, np.diff(prob["leaf_off"]))
+    for box in (0, min(5, lvl1.shape[0] - 1)):
+        sel = np.nonzero(leaf_owner == box)[0]
+        idx = np.ascontiguousarray(all_idx[:, sel])
+        c = lv[-2]["c"][:, box]
+        r = orc.moments("triangle", prob["vxyz"], idx, prob["sigma"], p, leaf_off=np.array([0, idx.shape[1]]),
+                        leaf_c=c.reshape(3, 1), density=1)
+        rb = np.max(np.linalg.norm(prob["vxyz"][:, np.unique(idx)] - c[:, None], axis=0))
+        assert norm_err(lvl1[box:box + 1], r, p, [rb], 0) <= tol
