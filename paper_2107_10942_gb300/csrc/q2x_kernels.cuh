@@ -269,19 +269,30 @@ __device__ __forceinline__ cf cf_zero()
 // c = x^m of degree n-1 and xi = X + iY,
 //   -xi a + eta b - z c + src = X (b - a) + (Y, -Y) * swap(a + b) - z c + src.
 // For m = 0 pass a = -conj(b): then -xi a + eta b = 2 Re(eta b) (Eq. (rec11))
-// and the imaginary part comes out exactly zero.
-__device__ __forceinline__ cf cf_stencil(cf a, cf b, cf c, cf src, cf X2, cf YmY, cf nZ2)
+// and the imaginary part comes out exactly zero.  The two neighbour
+// combinations are formed once per row entry and shared by every stencil
+// applied to it (the output level and its double layer).
+struct cf_nb {
+    cf d, sw;  // b - a and swap(a + b)
+};
+__device__ __forceinline__ cf_nb cf_neighbours(cf a, cf b)
 {
-    const cf d = cf_sub(b, a);
     // swap(a + b) with two scalar adds written straight into the swapped
     // halves (no register moves)
     float ar, ai, br, bi;
     cf_parts(a, ar, ai);
     cf_parts(b, br, bi);
-    const cf sw = cf_make(bi + ai, br + ar);
+    return cf_nb{cf_sub(b, a), cf_make(bi + ai, br + ar)};
+}
+__device__ __forceinline__ cf cf_stencil_nb(const cf_nb& nb, cf c, cf src, cf X2, cf YmY, cf nZ2)
+{
     cf t = cf_fma(nZ2, c, src);
-    t = cf_fma(X2, d, t);
-    return cf_fma(YmY, sw, t);
+    t = cf_fma(X2, nb.d, t);
+    return cf_fma(YmY, nb.sw, t);
+}
+__device__ __forceinline__ cf cf_stencil(cf a, cf b, cf c, cf src, cf X2, cf YmY, cf nZ2)
+{
+    return cf_stencil_nb(cf_neighbours(a, b), c, src, X2, YmY, nZ2);
 }
 
 // column c -> (n, m), exact for c < 2^20
@@ -883,9 +894,10 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                             const cf c = R[k][m];
                             const cf b = (m < P) ? R[k][m < P ? m + 1 : P] : cf_zero();
                             const cf a = (m == 0) ? cf_negconj(b) : pa[k];
+                            const cf_nb nbk = cf_neighbours(a, b);
                             if (KIND == KIND_TRI && k == OUT && want1) {
                                 // double layer from the output level's row n-1
-                                cf dl = cf_stencil(a, b, c, cf_zero(), XN2, YNm, nZN2);
+                                cf dl = cf_stencil_nb(nbk, c, cf_zero(), XN2, YNm, nZN2);
                                 float dr, di;
                                 cf_parts(dl, dr, di);
                                 if (st) {
@@ -904,7 +916,7 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                                 src = cf_fma(s1p, nw[3], nw[2]);  // E^ + s1 i^
                             else
                                 src = nw[k > 0 ? k - 1 : 0];
-                            nw[k] = cf_stencil(a, b, c, src, X2[k], YmY[k], nZ2[k]);
+                            nw[k] = cf_stencil_nb(nbk, c, src, X2[k], YmY[k], nZ2[k]);
                             pa[k] = c;
                             R[k][m] = nw[k];
                         }
