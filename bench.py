@@ -191,11 +191,11 @@ class ClockSampler:
 # ------------------------------------------------------------ reference arm
 
 def run_reference(args, rank, world):
+    if rank != 0:
+        return
     import oracle as orc
     prob = workload()
     cores = orc.max_threads()
-    if rank != 0:
-        return
     n = calibrate_sample(orc, prob, max(1.0, args.cpu_seconds / 3))
     sub = sub_problem(prob, sample_leaves(prob, n))
     ne = sub["idx"].shape[1]
