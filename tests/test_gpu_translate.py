@@ -123,3 +123,56 @@ def test_upward_pass_against_quadrature(q2x, orc, prec):
                         leaf_c=c.reshape(3, 1), density=1)
         rb = np.max(np.linalg.norm(prob["vxyz"][:, np.unique(idx)] - c[:, None], axis=0))
         assert norm_err(lvl1[box:box + 1], r, p, [rb], 0) <= tol
+
+
+def test_upward_pass_adaptive_mixed_ball(q2x, orc):
+    """Adaptive octree (leaves at depths 2 and 3) over segments, triangles and
+    tetrahedra: batch Q2X at the leaves (p = 8 everywhere), then the upward
+    pass; the root against the oracle's quadrature of all elements about the
+    cube centre, and every depth-1 box against quadrature over its elements."""
+    from paper_2107_10942_gb300.upward import Upward
+    p = 8
+    m = W.cfg_mixed_ball(n_fil=40, n_steps=100, tri_level=4, n_tri=3000, tet_spacing=0.2, n_tet=2500,
+                         max_per_leaf=300, max_depth=8, p_lo=p, p_hi=p, seed=11)
+    names = {"segment": "segments", "triangle": "triangles", "tetra": "tetra"}
+    kinds = {names[k]: {key: torch.from_numpy(v).cuda() for key, v in dd.items()} for k, dd in m["kinds"].items()}
+    plan = q2x.Plan(p, precision="fp64")
+    b = q2x.q2x.Batch(plan, torch.from_numpy(m["leaf_c"]).cuda(), torch.from_numpy(m["leaf_rho"]).cuda(),
+                      torch.from_numpy(m["leaf_p"]).cuda(), **kinds)
+    leaf = b.run()
+    up = Upward(plan, m["leaf_c"], -1.0, 2.0, m["leaf_depth"])
+    outs = up.run(leaf)
+    plan.sync()
+    assert len(set(m["leaf_depth"].tolist())) > 1
+
+    def quad(centre, leaf_sel):
+        ref = 0
+        for k, dd in m["kinds"].items():
+            o = dd["leaf_off"]
+            el = np.concatenate([np.arange(o[L], o[L + 1]) for L in leaf_sel]).astype(np.int64)
+            if len(el):
+                idx = np.ascontiguousarray(dd["idx"][:, el])
+                ref = ref + orc.moments(k, dd["vxyz"], idx, dd["sigma"][el], p, leaf_off=np.array([0, len(el)]),
+                                        leaf_c=centre.reshape(3, 1))
+        return ref
+
+    def radius(centre, leaf_sel):
+        r = 0.0
+        for dd in m["kinds"].values():
+            o = dd["leaf_off"]
+            el = np.concatenate([np.arange(o[L], o[L + 1]) for L in leaf_sel]).astype(np.int64)
+            if len(el):
+                v = dd["vxyz"][:, np.unique(dd["idx"][:, el])]
+                r = max(r, np.max(np.linalg.norm(v - centre[:, None], axis=0)))
+        return r
+
+    nl = m["leaf_c"].shape[1]
+    root = outs[-1].cpu().numpy()
+    c0 = np.zeros(3)
+    assert norm_err(root, quad(c0, range(nl)), p, [radius(c0, range(nl))], 0) <= 1e-12
+    # depth-1 boxes: the leaves inside each (by position)
+    lvl1 = outs[-2].cpu().numpy()
+    c1 = up.levels[-2]["c"]
+    for box in range(c1.shape[1]):
+        inside = np.nonzero(np.all(np.abs(m["leaf_c"] - c1[:, box:box + 1]) < 0.5, axis=0))[0]
+        assert norm_err(lvl1[box:box + 1], quad(c1[:, box], inside), p, [radius(c1[:, box], inside)], 0) <= 1e-12

@@ -357,7 +357,8 @@ def cfg_mixed_ball(n_fil=2000, n_steps=1000, step=1e-3, tri_level=9, n_tri=4_000
     split while it holds more than max_per_leaf elements of any kind, up to
     max_depth; per-leaf degree p_leaf ~ U{p_lo..p_hi}.
     Returns dict(kinds={segment, triangle, tetra: dict(vxyz, idx, sigma,
-    leaf_off)}, leaf_c, leaf_rho, leaf_p, p)."""
+    leaf_off)}, leaf_c, leaf_rho, leaf_p, leaf_depth, p); the octree cube is
+    [-1, 1]^3."""
     rng = np.random.default_rng(seed)
     kinds = {}
     vs, es = filaments(n_fil, n_steps, step, seed=seed + 1)
@@ -392,8 +393,9 @@ def cfg_mixed_ball(n_fil=2000, n_steps=1000, step=1e-3, tri_level=9, n_tri=4_000
         d["vxyz"] = np.ascontiguousarray(d["vxyz"], dtype=np.float64)
     rho = np.where(rho > 0, rho, 0.5 * np.sqrt(3.0) * leaf_h)
     leaf_p = rng.integers(p_lo, p_hi + 1, size=n_leaves).astype(np.int32)
+    leaf_depth = np.rint(np.log2(2.0 / leaf_h)).astype(np.int64)
     return dict(kinds=kinds, leaf_c=np.ascontiguousarray(leaf_c), leaf_rho=rho, leaf_p=leaf_p, p=int(p_hi),
-                name="mixed-ball")
+                leaf_depth=leaf_depth, name="mixed-ball")
 
 
 def cfg_sphere_adjoint(level: int = 8, n_tri: int = 1_000_000, depth: int = 6, p: int = 12, seed_shape: int = 5,
