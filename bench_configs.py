@@ -318,6 +318,47 @@ def run_upward(args, dev):
                             "%.2f s" % (prob["idx"].shape[1], dt), "kind": "oracle", "cores": orc.max_threads()}})
 
 
+def run_farfield(args, dev):
+    import paper_2107_10942_gb300 as q
+    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS
+    from paper_2107_10942_gb300.upward import Upward
+    import oracle as orc
+    p, depth, n_tgt = 12, 5, 1 << 20
+    prob = W.cfg_sphere_linear(level=7, depth=depth, p=p)
+    d = to_dev(prob, dev)
+    plan = q.Plan(p, precision="fp64")
+    leaf, _ = plan.triangles(d["vxyz"], d["idx"], d["sigma"], d["leaf_off"], d["leaf_c"], d["leaf_rho"], None,
+                             density="linear")
+    root = Upward(plan, d["leaf_c"], -1.125, 2.25, depth).run(leaf)[-1]
+    rng = np.random.default_rng(17)
+    tg = rng.normal(size=(3, n_tgt))
+    tg = 3.0 * tg / np.linalg.norm(tg, axis=0)
+    tgt = torch.from_numpy(tg).to(dev)
+    centre = torch.zeros((3, 1), dtype=torch.float64, device=dev)
+    out = torch.empty(n_tgt, dtype=torch.float64, device=dev)
+    off = torch.arange(n_tgt + 1, dtype=torch.int64, device=dev)
+    idx = torch.zeros(n_tgt, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ms = _time(lambda: plan.evaluate(root, centre, tgt, off, idx, out=out), args.steps, args.warmup, flush, stream)
+    got = out.cpu().numpy()
+    rc = root.cpu().numpy()[0]
+    plan.sync()
+    pick = rng.choice(n_tgt, 64, replace=False)
+    ref = orc.farfield(rc, np.zeros(3), tg[:, pick].T, p)[0]
+    err = float(np.max(np.abs(got[pick] - ref)) / np.max(np.abs(ref)))
+    flops = 28.0 * (p + 1) * (p + 2) / 2 * n_tgt
+    _emit({"metric": "far-field evaluations/s (one p=12 expansion per target)", "value": n_tgt / (ms * 1e-3),
+           "unit": "evaluations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "root expansion of the level-7 sphere (p=12, from Q2X + upward pass) at %d targets "
+                                  "on the radius-3 sphere" % n_tgt},
+           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
+                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP64_FLOPS,
+                        "flops_per_evaluation": 28 * (p + 1) * (p + 2) // 2},
+           "errors_vs_oracle": {"series": err, "sampled_targets": 64}})
+
+
 def to_dev(prob, dev):
     from paper_2107_10942_gb300.q2x import problem_to_device
     return problem_to_device({k: v for k, v in prob.items() if hasattr(v, "shape")}, dev)
@@ -328,5 +369,6 @@ def run(args):
     torch.cuda.set_device(dev)
     from paper_2107_10942_gb300 import build
     build.build()
-    {"icosphere-L3": run_icosphere_l3, "sphere-L9-const": run_sphere_l9, "upward": run_upward, "mixed-ball": run_mixed_ball,
+    {"icosphere-L3": run_icosphere_l3, "sphere-L9-const": run_sphere_l9, "upward": run_upward,
+     "far-field": run_farfield, "mixed-ball": run_mixed_ball,
      "sphere-L8-adjoint": run_adjoint}[args.config](args, dev)

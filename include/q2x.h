@@ -301,6 +301,25 @@ q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const double* sr
                          const double* src_c, int64_t n_dst, const int64_t* dst_off,
                          const double* dst_c, double* dst_coef, int accumulate);
 
+/* Far-field evaluation (the M2P step fed by the leaf or box coefficients):
+ * out[t] (+)= sum over the expansions e listed for target t of
+ *   phi_e(x_t) = sum_{n<=p} sum_{|m|<=n} F_n^m S_n^m(x_t - c_e)      (Eq. (bas3))
+ * with F the COEFF coefficients, or (1/4pi)(-1)^n M_n^{-m} for MOMENT
+ * coefficients (the plan's norm).  The value is real (Eq. (bas2.1)); the
+ * series converges for |x_t - c_e| larger than the expansion's radius, and
+ * an expansion evaluated exactly at its centre contributes 0.
+ *   coef     double[n_exp * (p+1)^2] packed (device); exp_c double[3 * n_exp] SoA
+ *   tgt      double[3 * n_tgt] SoA target points (device)
+ *   tgt_off  int64[n_tgt + 1] CSR into exp_idx (device); exp_idx int64 list of
+ *            expansion indices (device, non-NULL); an index out of range sets
+ *            the device error word (bit 1) and is skipped, a bad range sets bit 8
+ *   out      double[n_tgt] (device), overwritten or added to (accumulate = 1)
+ * FP64 arithmetic in both precisions of the plan; S_n^m by the
+ * associated-Legendre recurrences in Cartesian form (Eqs. (bas1)-(bas2)). */
+q2x_status q2x_evaluate(q2x_plan_t plan, int p, int64_t n_exp, const double* coef, const double* exp_c,
+                        int64_t n_tgt, const double* tgt, const int64_t* tgt_off, const int64_t* exp_idx,
+                        double* out, int accumulate);
+
 /* Segmented sum of per-element coefficient rows into leaves (Eq. (st4)):
  * coef[L] (+)= sum_{e in leaf L} elem[e], elem double[n_elem * (p+1)^2],
  * coef double[n_leaves * (p+1)^2], leaf_off as above (required).  FP64,

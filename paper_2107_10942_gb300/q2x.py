@@ -235,6 +235,36 @@ class Plan:
         return dst_coef
 
 
+    def evaluate(self, coef, exp_c, tgt, tgt_off=None, exp_idx=None, out=None, accumulate=False, p=None):
+        """Far-field potential at the targets tgt (3, n_tgt) of the expansions
+        (coef rows about exp_c) listed per target by the CSR tgt_off/exp_idx
+        (default: every target evaluates every expansion).  q2x_evaluate."""
+        p = self.p_max if p is None else int(p)
+        nc = n_coef(p)
+        _need(coef, torch.float64, "coef")
+        if coef.dim() != 2 or coef.shape[1] != nc:
+            raise ValueError("coef must be (n_exp, (p+1)^2)")
+        n_exp = coef.shape[0]
+        _need(exp_c, torch.float64, "exp_c", (3, n_exp))
+        _need(tgt, torch.float64, "tgt")
+        if tgt.dim() != 2 or tgt.shape[0] != 3:
+            raise ValueError("tgt must be (3, n_tgt)")
+        n_tgt = tgt.shape[1]
+        if tgt_off is None:
+            tgt_off = torch.arange(n_tgt + 1, dtype=torch.int64, device=tgt.device) * n_exp
+            exp_idx = torch.arange(n_exp, dtype=torch.int64, device=tgt.device).repeat(n_tgt)
+        _need(tgt_off, torch.int64, "tgt_off", (n_tgt + 1,))
+        _need(exp_idx, torch.int64, "exp_idx")
+        if out is None:
+            if accumulate:
+                raise ValueError("accumulate=True needs an output tensor")
+            out = torch.empty(n_tgt, dtype=torch.float64, device=tgt.device)
+        _need(out, torch.float64, "out", (n_tgt,))
+        check(lib().q2x_evaluate(self._h, p, n_exp, _ptr(coef), _ptr(exp_c), n_tgt, _ptr(tgt), _ptr(tgt_off),
+                                 _ptr(exp_idx), _ptr(out), int(bool(accumulate))), self._h)
+        return out
+
+
 def problem_to_device(prob: dict, device="cuda") -> dict:
     """Copy a workloads-style problem dict (numpy arrays) to device tensors."""
     out = {}
