@@ -359,6 +359,46 @@ def run_farfield(args, dev):
            "errors_vs_oracle": {"series": err, "sampled_targets": 64}})
 
 
+def run_galerkin(args, dev):
+    import paper_2107_10942_gb300 as q
+    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS, element_flops
+    import oracle as orc
+    p, depth = 12, 5
+    prob = W.cfg_sphere_linear(level=7, depth=depth, p=p)
+    d = to_dev(prob, dev)
+    nl = prob["leaf_c"].shape[1]
+    n_elem = prob["idx"].shape[1]
+    w = torch.from_numpy(np.random.default_rng(21).standard_normal((nl, (p + 1) ** 2))).to(dev)
+    ones = torch.ones(n_elem, dtype=torch.float64, device=dev)
+    out = torch.empty(n_elem, dtype=torch.float64, device=dev)
+    plan = q.Plan(p, norm="moment", precision="fp64")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    run = lambda: plan.galerkin_triangles(d["vxyz"], d["idx"], w, d["leaf_off"], d["leaf_c"], d["leaf_rho"],
+                                          sigma=ones, layer=0, out=out)
+    ms = _time(run, args.steps, args.warmup, flush, stream)
+    got = out.cpu().numpy()
+    plan.sync()
+    # sampled elements against the oracle's per-element moments contracted with w
+    rng = np.random.default_rng(22)
+    el = np.sort(rng.choice(n_elem, 200, replace=False))
+    leaf_of = np.repeat(np.arange(nl), np.diff(prob["leaf_off"]))
+    P = orc.moments("triangle", prob["vxyz"], np.ascontiguousarray(prob["idx"][:, el]), np.ones(len(el)), p,
+                    leaf_off=None, leaf_c=np.ascontiguousarray(prob["leaf_c"][:, leaf_of[el]]), norm=1)
+    wn = w.cpu().numpy()
+    ref = np.sum(P * wn[leaf_of[el]], axis=1)
+    err = float(np.max(np.abs(got[el] - ref) / np.sum(np.abs(P * wn[leaf_of[el]]), axis=1)))
+    flops = (element_flops("triangle", "const", ("single",), p) + (p + 1) ** 2) * n_elem
+    _emit({"metric": "Galerkin element integrals/s (local expansion over each receiving triangle)",
+           "value": n_elem / (ms * 1e-3), "unit": "elements/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "the level-7 sphere's %d triangles against random local expansions of its %d "
+                                  "depth-5 leaves, p=12, single layer" % (n_elem, nl)},
+           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
+                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP64_FLOPS},
+           "errors_vs_oracle": {"relative_to_sum_of_terms": err, "sampled_elements": 200}})
+
+
 def to_dev(prob, dev):
     from paper_2107_10942_gb300.q2x import problem_to_device
     return problem_to_device({k: v for k, v in prob.items() if hasattr(v, "shape")}, dev)
@@ -370,5 +410,5 @@ def run(args):
     from paper_2107_10942_gb300 import build
     build.build()
     {"icosphere-L3": run_icosphere_l3, "sphere-L9-const": run_sphere_l9, "upward": run_upward,
-     "far-field": run_farfield, "mixed-ball": run_mixed_ball,
+     "far-field": run_farfield, "galerkin": run_galerkin, "mixed-ball": run_mixed_ball,
      "sphere-L8-adjoint": run_adjoint}[args.config](args, dev)

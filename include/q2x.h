@@ -320,6 +320,29 @@ q2x_status q2x_evaluate(q2x_plan_t plan, int p, int64_t n_exp, const double* coe
                         int64_t n_tgt, const double* tgt, const int64_t* tgt_off, const int64_t* exp_idx,
                         double* out, int accumulate);
 
+/* Receiver-side (Galerkin) integration over triangles: for every triangle e
+ * of leaf L,
+ *   out[e] = sum_c w[L][c] P_c(e),
+ * P(e) the packed coefficients of triangle e alone with constant density
+ * sigma[e] (layer 0: single layer, Eq. (bas4); layer 1: double layer, with
+ * n.grad) in the plan's norm, about leaf L's centre, up to the plan's p_max.
+ * With the MOMENT norm and the weights of a local expansion
+ * phi(y) = sum_{n,m} L_n^m R_n^m(y - c) (w = L_n^0 at (n, 0), 2 Re L_n^m at
+ * (n, m > 0), -2 Im L_n^m at (n, -m)), out[e] is the integral of
+ * sigma[e] phi (layer 0) or sigma[e] n.grad phi (layer 1) over the triangle,
+ * i.e. the receiving side of a Galerkin boundary-element FMM.  Computed by
+ * the same recursions as the Q2X element kernels (Lemmas 2-3), contracted per
+ * element instead of summed per leaf.
+ *   vxyz, idx, sigma, leaf_off, leaf_c, leaf_rho: as q2x_triangles_single
+ *   (sigma required: the per-element weights)
+ *   w    double[n_leaves * (p_max+1)^2] (device)
+ *   out  double[n_elem] (device), overwritten
+ * FP64 arithmetic in both precisions of the plan; deterministic. */
+q2x_status q2x_galerkin_triangles(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const double* vxyz,
+                                  const int32_t* idx, const double* sigma, int64_t n_leaves,
+                                  const int64_t* leaf_off, const double* leaf_c, const double* leaf_rho,
+                                  int layer, const double* w, double* out);
+
 /* Segmented sum of per-element coefficient rows into leaves (Eq. (st4)):
  * coef[L] (+)= sum_{e in leaf L} elem[e], elem double[n_elem * (p+1)^2],
  * coef double[n_leaves * (p+1)^2], leaf_off as above (required).  FP64,

@@ -265,6 +265,43 @@ class Plan:
         return out
 
 
+    def galerkin_triangles(self, vxyz, idx, weights, leaf_off, leaf_c, leaf_rho=None, sigma=None, layer=0,
+                           out=None):
+        """Per-triangle contraction sum_c weights[L][c] P_c(e) of each
+        triangle's own packed coefficients (q2x_galerkin_triangles); with a
+        MOMENT plan and local_expansion_weights(L) it integrates the local
+        expansion over each triangle (layer 0) or its normal derivative
+        (layer 1).  sigma: per-triangle weights (default 1)."""
+        n_vert, n_elem = self._geom(vxyz, idx, 3)
+        n_leaves = self._leaf_args(n_elem, leaf_off, leaf_c, leaf_rho, None)
+        _need(weights, torch.float64, "weights", (n_leaves, n_coef(self.p_max)))
+        if sigma is None:
+            sigma = torch.ones(n_elem, dtype=torch.float64, device=vxyz.device)
+        _need(sigma, torch.float64, "sigma", (n_elem,))
+        if out is None:
+            out = torch.empty(n_elem, dtype=torch.float64, device=vxyz.device)
+        _need(out, torch.float64, "out", (n_elem,))
+        check(lib().q2x_galerkin_triangles(self._h, n_elem, n_vert, _ptr(vxyz), _ptr(idx), _ptr(sigma), n_leaves,
+                                           _ptr(leaf_off), _ptr(leaf_c), _ptr(leaf_rho), int(layer), _ptr(weights),
+                                           _ptr(out)), self._h)
+        return out
+
+
+def local_expansion_weights(L_re, L_im, p):
+    """Packed Galerkin weights of local expansions phi(y) = sum L_n^m R_n^m(y-c)
+    given by the real and imaginary parts of L_n^m for m >= 0 (tensors
+    (..., (p+1)^2) indexed k = n*n+n+m with m >= 0 used): L_n^0 at (n, 0),
+    2 Re L_n^m at (n, m), -2 Im L_n^m at (n, -m)."""
+    w = torch.zeros_like(L_re)
+    for n in range(p + 1):
+        k0 = n * n + n
+        w[..., k0] = L_re[..., k0]
+        for m in range(1, n + 1):
+            w[..., k0 + m] = 2.0 * L_re[..., k0 + m]
+            w[..., k0 - m] = -2.0 * L_im[..., k0 + m]
+    return w
+
+
 def problem_to_device(prob: dict, device="cuda") -> dict:
     """Copy a workloads-style problem dict (numpy arrays) to device tensors."""
     out = {}
