@@ -399,6 +399,54 @@ def run_galerkin(args, dev):
            "errors_vs_oracle": {"relative_to_sum_of_terms": err, "sampled_elements": 200}})
 
 
+def run_biot_savart(args, dev):
+    import paper_2107_10942_gb300 as q
+    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS, element_flops
+    from paper_2107_10942_gb300.upward import Upward
+    p = 12
+    m = W.cfg_mixed_ball()
+    sg = m["kinds"]["segment"]
+    vx, idx = sg["vxyz"], sg["idx"]
+    # vortex-filament currents: strength sigma along each segment's direction
+    tang = vx[:, idx[1]] - vx[:, idx[0]]
+    cur = sg["sigma"] * tang / np.linalg.norm(tang, axis=0)
+    n_elem = idx.shape[1]
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in
+         dict(vxyz=vx, idx=idx, cur=cur, leaf_off=sg["leaf_off"], leaf_c=m["leaf_c"], leaf_rho=m["leaf_rho"]).items()}
+    plan = q.Plan(p, precision="fp64")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ms_q2x = _time(lambda: plan.segments_vector(d["vxyz"], d["idx"], d["cur"], d["leaf_off"], d["leaf_c"],
+                                                d["leaf_rho"]), args.steps, args.warmup, flush, stream)
+    c3 = plan.segments_vector(d["vxyz"], d["idx"], d["cur"], d["leaf_off"], d["leaf_c"], d["leaf_rho"])
+    up = Upward(plan, m["leaf_c"], -1.0, 2.0, m["leaf_depth"])
+    root3 = torch.stack([up.run(c3[k].contiguous())[-1] for k in range(3)]).contiguous()
+    n_tgt = 1 << 18
+    tg = np.random.default_rng(5).normal(size=(3, n_tgt))
+    tgt = torch.from_numpy(2.0 * tg / np.linalg.norm(tg, axis=0)).to(dev)
+    centre = torch.zeros((3, 1), dtype=torch.float64, device=dev)
+    off = torch.arange(n_tgt + 1, dtype=torch.int64, device=dev)
+    eidx = torch.zeros(n_tgt, dtype=torch.int64, device=dev)
+    H = torch.empty((3, n_tgt), dtype=torch.float64, device=dev)
+    ms_curl = _time(lambda: plan.evaluate_curl(root3, centre, tgt, off, eidx, out=H), args.steps, args.warmup,
+                    flush, stream)
+    plan.sync()
+    per_step = 3 * n_elem * (p + 1) ** 2
+    flops = 3 * element_flops("segment", "const", ("single",), p) * n_elem
+    _emit({"metric": "vector line-density Q2X element-moments/s (three components, Eq. st3)",
+           "value": per_step / (ms_q2x * 1e-3), "unit": "element-moments/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_q2x, "higher_is_better": True, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "the mixed ball's %d filament segments with vortex currents along them, %d "
+                                  "adaptive leaves, p=12 (one segment pass per component)" % (n_elem,
+                                                                                           m["leaf_c"].shape[1])},
+           "roofline": {"bound": "alu", "achieved": flops / (ms_q2x * 1e-3) / 1e12,
+                        "peak": PEAK_FP64_FLOPS / 1e12, "unit": "TFLOP/s",
+                        "frac": flops / (ms_q2x * 1e-3) / PEAK_FP64_FLOPS},
+           "curl_evaluation": {"targets": n_tgt, "ms": ms_curl, "value": n_tgt / (ms_curl * 1e-3),
+                               "unit": "H evaluations/s (root expansion, p=12, radius 2)"}})
+
+
 def to_dev(prob, dev):
     from paper_2107_10942_gb300.q2x import problem_to_device
     return problem_to_device({k: v for k, v in prob.items() if hasattr(v, "shape")}, dev)
@@ -410,5 +458,5 @@ def run(args):
     from paper_2107_10942_gb300 import build
     build.build()
     {"icosphere-L3": run_icosphere_l3, "sphere-L9-const": run_sphere_l9, "upward": run_upward,
-     "far-field": run_farfield, "galerkin": run_galerkin, "mixed-ball": run_mixed_ball,
+     "far-field": run_farfield, "galerkin": run_galerkin, "biot-savart": run_biot_savart, "mixed-ball": run_mixed_ball,
      "sphere-L8-adjoint": run_adjoint}[args.config](args, dev)

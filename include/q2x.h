@@ -320,6 +320,21 @@ q2x_status q2x_evaluate(q2x_plan_t plan, int p, int64_t n_exp, const double* coe
                         int64_t n_tgt, const double* tgt, const int64_t* tgt_off, const int64_t* exp_idx,
                         double* out, int accumulate);
 
+/* Curl of the far field of vector expansions (Biot-Savart, Eq. (st3)):
+ * expansion e has three component rows F^(k) (k = x, y, z), e.g. segment
+ * coefficients computed with the components of a vector line density as
+ * sigma; A_k(x) = sum_{n,m} F^(k)_n^m S_n^m(x - c_e) and
+ *   out3[d][t] (+)= (curl A)_d at target t, summed over the listed expansions,
+ * i.e. H(x) = (1/4pi) int I x (x - y)/|x - y|^3 dl for line currents I.
+ *   coef3   double[3 * n_exp * (p+1)^2]: component-major [3][n_exp][np] (device)
+ *   out3    double[3 * n_tgt] SoA (device)
+ * Other arguments as q2x_evaluate.  The gradients of S_n^m are carried
+ * through the same recurrences in forward mode (no derivative tables).  COEFF
+ * norm only (Q2X_ERR_UNSUPPORTED otherwise).  FP64. */
+q2x_status q2x_evaluate_curl(q2x_plan_t plan, int p, int64_t n_exp, const double* coef3, const double* exp_c,
+                             int64_t n_tgt, const double* tgt, const int64_t* tgt_off, const int64_t* exp_idx,
+                             double* out3, int accumulate);
+
 /* Receiver-side (Galerkin) integration over triangles: for every triangle e
  * of leaf L,
  *   out[e] = sum_c w[L][c] P_c(e),

@@ -146,7 +146,158 @@ __global__ void q2x_evaluate_kernel(const EvalArgs a)
     a.out[t] = a.accumulate ? a.out[t] + acc : acc;
 }
 
+// ---------------------------------------------------------------- curl
+// A value and its gradient (forward-mode derivative in x, y, z): the far-field
+// recurrences above are rational in (x, y, z), so carrying gradients through
+// them gives grad S_n^m exactly (to rounding), with no separate formulas.
+struct D4 {
+    double v, x, y, z;
+};
+__device__ __forceinline__ D4 d4(double v) { return D4{v, 0.0, 0.0, 0.0}; }
+__device__ __forceinline__ D4 operator+(D4 a, D4 b) { return D4{a.v + b.v, a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ D4 operator-(D4 a, D4 b) { return D4{a.v - b.v, a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ D4 operator*(double s, D4 a) { return D4{s * a.v, s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ D4 operator*(D4 a, D4 b)
+{
+    return D4{a.v * b.v, fma(a.v, b.x, a.x * b.v), fma(a.v, b.y, a.y * b.v), fma(a.v, b.z, a.z * b.v)};
+}
+
+// Gradients of the three component series A_k(x) = sum F^(k)_n^m S_n^m(x - c)
+// at offset (x, y, z): g[k] += grad A_k.  F3 holds the three packed rows of
+// one expansion, `stride` apart (COEFF norm).
+__device__ void grad_one(const double* __restrict__ F3, int64_t stride, int p, double x, double y, double z,
+                         double g[3][3])
+{
+    const double r2v = x * x + y * y + z * z;
+    if (!(r2v > 0.0)) return;
+    const D4 X{x, 1.0, 0.0, 0.0}, Y{y, 0.0, 1.0, 0.0}, Z{z, 0.0, 0.0, 1.0};
+    const D4 r2 = X * X + Y * Y + Z * Z;
+    // 1/r^2 and 1/r with their gradients: d(1/r2) = -dr2 / r2^2, d(r^-1) = -(1/2) r^-3 dr2
+    const double ir2v = 1.0 / r2v, irv = sqrt(ir2v);
+    const D4 ir2{ir2v, -r2.x * ir2v * ir2v, -r2.y * ir2v * ir2v, -r2.z * ir2v * ir2v};
+    const double c = -0.5 * irv * ir2v;
+    const D4 ir{irv, c * r2.x, c * r2.y, c * r2.z};
+    D4 tmr = d4(1.0), tmi = d4(0.0);
+#pragma unroll 1
+    for (int m = 0; m <= p; ++m) {
+        if (m > 0) {
+            const double f = -(double)(2 * m - 1);
+            const D4 nr = f * (X * tmr - Y * tmi);
+            const D4 ni = f * (X * tmi + Y * tmr);
+            tmr = nr;
+            tmi = ni;
+        }
+        double rot_r, rot_i;
+        switch (m & 3) {
+            case 0: rot_r = 1.0; rot_i = 0.0; break;
+            case 1: rot_r = 0.0; rot_i = -1.0; break;
+            case 2: rot_r = -1.0; rot_i = 0.0; break;
+            default: rot_r = 0.0; rot_i = 1.0; break;
+        }
+        D4 t2r = d4(0.0), t2i = d4(0.0);
+        D4 t1r = tmr, t1i = tmi;
+        D4 irp = ir;
+        for (int j = 0; j < m; ++j) irp = irp * ir2;
+        const double w = m ? 2.0 : 1.0;
+#pragma unroll 1
+        for (int n = m; n <= p; ++n) {
+            D4 tr, ti;
+            if (n == m) {
+                tr = t1r;
+                ti = t1i;
+            } else {
+                const double a = (double)(2 * n - 1), b = (double)(n + m - 1), inv = c_fact.inv[n - m];
+                tr = inv * (a * (Z * t1r) - b * (r2 * t2r));
+                ti = inv * (a * (Z * t1i) - b * (r2 * t2i));
+                t2r = t1r;
+                t2i = t1i;
+                t1r = tr;
+                t1i = ti;
+                irp = irp * ir2;
+            }
+            const D4 sc = c_fact.v[n - m] * irp;
+            const D4 sr = sc * (rot_r * tr - rot_i * ti);
+            const D4 si = sc * (rot_r * ti + rot_i * tr);
+            const int k0 = n * n + n;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double cr = __ldg(F3 + k * stride + k0 + m);
+                const double ci = m ? __ldg(F3 + k * stride + k0 - m) : 0.0;
+                g[k][0] += w * (cr * sr.x - ci * si.x);
+                g[k][1] += w * (cr * sr.y - ci * si.y);
+                g[k][2] += w * (cr * sr.z - ci * si.z);
+            }
+        }
+    }
+}
+
+// H = curl A at each target (Eq. (st3)): expansions with three component rows.
+__global__ void q2x_evaluate_curl_kernel(const EvalArgs a)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_tgt) return;
+    int64_t j0 = __ldg(a.tgt_off + t), j1 = __ldg(a.tgt_off + t + 1);
+    if (j0 < 0 || j1 < j0) {
+        atomicOr(a.err, 8u);
+        j0 = j1 = 0;
+    }
+    const double x = __ldg(a.tgt + t), y = __ldg(a.tgt + a.n_tgt + t), z = __ldg(a.tgt + 2 * a.n_tgt + t);
+    double g[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};  // g[k][j] = d A_k / d x_j
+#pragma unroll 1
+    for (int64_t j = j0; j < j1; ++j) {
+        const int64_t e = __ldg(a.exp_idx + j);
+        if (e < 0 || e >= a.n_exp) {
+            atomicOr(a.err, 1u);
+            continue;
+        }
+        grad_one(a.coef + e * (int64_t)a.np, a.n_exp * (int64_t)a.np, a.p, x - __ldg(a.exp_c + e),
+                 y - __ldg(a.exp_c + a.n_exp + e), z - __ldg(a.exp_c + 2 * a.n_exp + e), g);
+    }
+    const double h[3] = {g[2][1] - g[1][2], g[0][2] - g[2][0], g[1][0] - g[0][1]};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double* o = a.out + d * a.n_tgt + t;
+        *o = a.accumulate ? *o + h[d] : h[d];
+    }
+}
+
 }  // namespace q2x
+
+extern "C" q2x_status q2x_evaluate_curl(q2x_plan_t plan, int p, int64_t n_exp, const double* coef3,
+                                        const double* exp_c, int64_t n_tgt, const double* tgt,
+                                        const int64_t* tgt_off, const int64_t* exp_idx, double* out3,
+                                        int accumulate)
+{
+    if (!plan) return q2x_fail(nullptr, Q2X_ERR_ARG, "plan is NULL");
+    if (plan->norm != 0) return q2x_fail(plan, Q2X_ERR_UNSUPPORTED, "curl evaluation needs the COEFF norm");
+    if (p < 0 || p > plan->p_max) return q2x_fail(plan, Q2X_ERR_RANGE, "p = %d outside 0..%d", p, plan->p_max);
+    if (n_exp < 0 || n_tgt < 0) return q2x_fail(plan, Q2X_ERR_ARG, "negative size");
+    if (accumulate != 0 && accumulate != 1) return q2x_fail(plan, Q2X_ERR_ARG, "accumulate must be 0 or 1");
+    if (n_tgt == 0) return Q2X_OK;
+    if (!tgt || !tgt_off || !exp_idx || !out3) return q2x_fail(plan, Q2X_ERR_ARG, "NULL target array");
+    if (n_exp > 0 && (!coef3 || !exp_c)) return q2x_fail(plan, Q2X_ERR_ARG, "NULL expansion array");
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "cudaSetDevice");
+    q2x::EvalArgs a;
+    a.p = p;
+    a.np = (p + 1) * (p + 1);
+    a.norm = 0;
+    a.accumulate = accumulate;
+    a.n_exp = n_exp;
+    a.n_tgt = n_tgt;
+    a.coef = coef3;
+    a.exp_c = exp_c;
+    a.tgt = tgt;
+    a.tgt_off = tgt_off;
+    a.exp_idx = exp_idx;
+    a.out = out3;
+    a.err = plan->d_err;
+    q2x::q2x_evaluate_curl_kernel<<<(unsigned)((n_tgt + 127) / 128), 128, 0, plan->stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "q2x_evaluate_curl_kernel launch");
+    plan->launches += 1;
+    return Q2X_OK;
+}
 
 extern "C" q2x_status q2x_evaluate(q2x_plan_t plan, int p, int64_t n_exp, const double* coef, const double* exp_c,
                                    int64_t n_tgt, const double* tgt, const int64_t* tgt_off,

@@ -265,6 +265,47 @@ class Plan:
         return out
 
 
+    def segments_vector(self, vxyz, idx, current, leaf_off, leaf_c, leaf_rho=None, leaf_p=None):
+        """Coefficients of the three components of a vector line density
+        (current (3, n_elem), constant per segment), as (3, n_leaves,
+        (p+1)^2): one segment pass per component (Eq. (st3): the moments are
+        geometric and multiply each component)."""
+        _need(current, torch.float64, "current", (3, idx.shape[1]))
+        n_leaves = leaf_c.shape[1]
+        out = torch.empty((3, n_leaves, n_coef(self.p_max)), dtype=torch.float64, device=vxyz.device)
+        for k in range(3):
+            self.segments(vxyz, idx, current[k].contiguous(), leaf_off, leaf_c, leaf_rho, leaf_p, coef=out[k])
+        return out
+
+    def evaluate_curl(self, coef3, exp_c, tgt, tgt_off=None, exp_idx=None, out=None, accumulate=False, p=None):
+        """curl of the far field of vector expansions coef3 (3, n_exp,
+        (p+1)^2) about exp_c at the targets (3, n_tgt): the Biot-Savart field
+        H of Eq. (st3) for line currents (q2x_evaluate_curl).  Returns (3, n_tgt)."""
+        p = self.p_max if p is None else int(p)
+        nc = n_coef(p)
+        _need(coef3, torch.float64, "coef3")
+        if coef3.dim() != 3 or coef3.shape[0] != 3 or coef3.shape[2] != nc:
+            raise ValueError("coef3 must be (3, n_exp, (p+1)^2)")
+        n_exp = coef3.shape[1]
+        _need(exp_c, torch.float64, "exp_c", (3, n_exp))
+        _need(tgt, torch.float64, "tgt")
+        if tgt.dim() != 2 or tgt.shape[0] != 3:
+            raise ValueError("tgt must be (3, n_tgt)")
+        n_tgt = tgt.shape[1]
+        if tgt_off is None:
+            tgt_off = torch.arange(n_tgt + 1, dtype=torch.int64, device=tgt.device) * n_exp
+            exp_idx = torch.arange(n_exp, dtype=torch.int64, device=tgt.device).repeat(n_tgt)
+        _need(tgt_off, torch.int64, "tgt_off", (n_tgt + 1,))
+        _need(exp_idx, torch.int64, "exp_idx")
+        if out is None:
+            if accumulate:
+                raise ValueError("accumulate=True needs an output tensor")
+            out = torch.empty((3, n_tgt), dtype=torch.float64, device=tgt.device)
+        _need(out, torch.float64, "out", (3, n_tgt))
+        check(lib().q2x_evaluate_curl(self._h, p, n_exp, _ptr(coef3), _ptr(exp_c), n_tgt, _ptr(tgt),
+                                      _ptr(tgt_off), _ptr(exp_idx), _ptr(out), int(bool(accumulate))), self._h)
+        return out
+
     def galerkin_triangles(self, vxyz, idx, weights, leaf_off, leaf_c, leaf_rho=None, sigma=None, layer=0,
                            out=None):
         """Per-triangle contraction sum_c weights[L][c] P_c(e) of each
