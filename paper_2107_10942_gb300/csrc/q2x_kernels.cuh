@@ -1080,8 +1080,6 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
 {
     using C = Chain<KIND, DENS>;
     constexpr int NL = C::NL;
-    constexpr int OUT = NL - 1;
-    constexpr int NV = KIND + 2;
     constexpr int CH = KCfg<T>::CHUNK, LD = KCfg<T>::LD;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
