@@ -13,8 +13,9 @@
 //
 // Two kernels: one warp per source unpacks the source row to complex values
 // in shared memory, builds R(t) there and writes the translated row (outputs
-// n, m >= 0); one warp per destination then adds its sources' rows in source
-// order (deterministic) and packs them.  FP64.
+// n, m >= 0) from a flattened term schedule that gives every lane the same
+// work; one warp per destination then adds its sources' rows in source order
+// (deterministic) and packs them.  FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,11 +28,10 @@
 namespace q2x {
 
 constexpr int TR_WARPS = 4;
-constexpr int TR_MAX_OUT_PER_LANE = ((Q2X_P_MAX + 1) * (Q2X_P_MAX + 2) / 2 + 31) / 32;  // 8
 
 struct TransArgs {
     int p, np, n_out, norm, accumulate;
-    int wps, wps_log2;  // warps per source (a power of two; splits one translation's outputs)
+    int cta_per_source;  // 1: the four warps of a CTA share one source's terms
     int64_t n_src, n_dst;
     const double* src_coef;
     const double* src_c;
@@ -63,20 +63,82 @@ constexpr InvN make_inv_n()
 }
 static __constant__ InvN c_inv_n = make_inv_n();
 
-// wps warps per source: each builds the source's complex row and R(t) and
-// writes the translated outputs o = sub*32 + lane + 32*wps*i of its share.
+// Term schedule of the contraction: every (output o = n(n+1)/2 + m, k, l)
+// term in output order, for p up to Q2X_P_MAX (the terms of degrees <= p
+// are a prefix).  Code: bits 0-9 the R row index k^2 + k + l, plus
+// Q2X_P_MAX's (p+1)^2 when the term carries the COEFF sign (-1)^k (the warp
+// keeps -R there); bits 10-18 the F row index; bits 19-26 the output o.
+constexpr int TR_NP_MAX = (Q2X_P_MAX + 1) * (Q2X_P_MAX + 1);
+constexpr int tr_term_count(int p)
+{
+    int t = 0;
+    for (int n = 0; n <= p; ++n)
+        for (int m = 0; m <= n; ++m)
+            for (int k = 0; k <= n; ++k) {
+                const int nn = n - k;
+                const int l0 = (-k > -nn - m) ? -k : -nn - m, l1 = (k < nn - m) ? k : nn - m;
+                if (l1 >= l0) t += l1 - l0 + 1;
+            }
+    return t;
+}
+constexpr int TR_TERMS = tr_term_count(Q2X_P_MAX);
+struct TermTab {
+    uint32_t code[2][TR_TERMS];  // [norm]
+    int end[Q2X_P_MAX + 1];      // terms of degrees <= p: [0, end[p])
+};
+constexpr TermTab make_terms()
+{
+    TermTab tt{};
+    for (int norm = 0; norm < 2; ++norm) {
+        int t = 0;
+        for (int n = 0; n <= Q2X_P_MAX; ++n) {
+            for (int m = 0; m <= n; ++m) {
+                const int o = n * (n + 1) / 2 + m;
+                for (int k = 0; k <= n; ++k) {
+                    const int nn = n - k;
+                    int l0 = 0, l1 = -1;
+                    if (norm == 0) {  // F_{n-k}^{m+l}
+                        l0 = (-k > -nn - m) ? -k : -nn - m;
+                        l1 = (k < nn - m) ? k : nn - m;
+                    } else {  // M_{n-k}^{m-l}
+                        l0 = (-k > m - nn) ? -k : m - nn;
+                        l1 = (k < m + nn) ? k : m + nn;
+                    }
+                    for (int l = l0; l <= l1; ++l) {
+                        const int ri = k * k + k + l + ((norm == 0 && (k & 1)) ? TR_NP_MAX : 0);
+                        const int fi = nn * nn + nn + (norm == 0 ? m + l : m - l);
+                        tt.code[norm][t++] = (uint32_t)ri | ((uint32_t)fi << 10) | ((uint32_t)o << 19);
+                    }
+                }
+            }
+            if (norm == 0) tt.end[n] = t;
+        }
+    }
+    return tt;
+}
+static __device__ const TermTab g_terms = make_terms();
+
+// One warp per source (or, for the few sources at the top of a tree, one
+// CTA of four warps per source): the source's complex row and R(t) (and
+// -R(t)) in each warp's shared memory, then the contraction over the
+// flattened term list, each lane a contiguous run of terms (equal work per
+// lane).  Outputs wholly inside a lane's run are written by that lane; the
+// partial sums of the outputs at run boundaries are added in run order by
+// the first thread of the warp (or CTA).
 __global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int64_t gw = (int64_t)blockIdx.x * TR_WARPS + wib;
-    const int64_t s = gw >> a.wps_log2;
-    const int sub = (int)(gw & (a.wps - 1));
+    const int64_t s = a.cta_per_source ? (int64_t)blockIdx.x : (int64_t)blockIdx.x * TR_WARPS + wib;
+    const int nsub = a.cta_per_source ? TR_WARPS : 1;  // runs of 32 lanes sharing the source
+    const int sub = a.cta_per_source ? wib : 0;
     if (s >= a.n_src) return;
-    const int p = a.p, np = a.np, n_out = a.n_out;
-    double2* Fc = reinterpret_cast<double2*>(smem_raw) + (size_t)wib * 2 * np;
-    double2* Rc = Fc + np;
+    const int p = a.p, np = a.np;
+    double2* Fc = reinterpret_cast<double2*>(smem_raw) + (size_t)wib * 3 * TR_NP_MAX;
+    double2* Rc = Fc + TR_NP_MAX;  // R at [0, TR_NP_MAX), -R at [TR_NP_MAX, 2 TR_NP_MAX)
+    __shared__ int s_head_o[TR_WARPS][32], s_tail_o[TR_WARPS][32];
+    __shared__ double2 s_head_v[TR_WARPS][32], s_tail_v[TR_WARPS][32];
     // destination of s: the range of dst_off holding it (clamped; ranges are
     // validated by the combine kernel)
     int64_t lo = 0, hi = a.n_dst - 1;
@@ -107,7 +169,10 @@ __global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransA
     const double tx = __ldg(a.src_c + s) - __ldg(a.dst_c + d);
     const double ty = __ldg(a.src_c + a.n_src + s) - __ldg(a.dst_c + a.n_dst + d);
     const double tz = __ldg(a.src_c + 2 * a.n_src + s) - __ldg(a.dst_c + 2 * a.n_dst + d);
-    if (lane == 0) Rc[0] = make_double2(1.0, 0.0);
+    if (lane == 0) {
+        Rc[0] = make_double2(1.0, 0.0);
+        Rc[TR_NP_MAX] = make_double2(-1.0, 0.0);
+    }
     __syncwarp();
     // i xi = (-y + i x)/2, i eta = (y + i x)/2
     const double ixr = -0.5 * ty, ixi = 0.5 * tx;
@@ -133,58 +198,76 @@ __global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransA
                 v.x -= tz * r.x;
                 v.y -= tz * r.y;
             }
-            Rc[n * n + n + m] = make_double2(v.x * inv, v.y * inv);
+            const double2 rv = make_double2(v.x * inv, v.y * inv);
+            Rc[n * n + n + m] = rv;
+            Rc[TR_NP_MAX + n * n + n + m] = make_double2(-rv.x, -rv.y);
         }
         __syncwarp();
     }
-    // ---- contraction: lane takes outputs lane, lane + 32, ... (mixed degrees)
-    double2* row = a.rows + s * (int64_t)n_out;
-    // F index step along l: +1 for COEFF (F_{n-k}^{m+l}), -1 for MOMENT (M_{n-k}^{m-l})
-    const int fs = (a.norm == 0) ? 1 : -1;
-    // outputs are visited in "snake" order over the lanes (lane L of a block
-    // of 64 takes L and 63 - L), pairing costly high degrees with cheap low
-    // ones; the warps of a source take interleaved blocks
-    const int stride = 32 * a.wps;
+    // ---- contraction over this lane's run of terms
+    double2* row = a.rows + s * (int64_t)a.n_out;
+    const uint32_t* code = g_terms.code[a.norm ? 1 : 0];
+    const int T = g_terms.end[p];
+    const int C = (T + 32 * nsub - 1) / (32 * nsub);
+    const int t0 = min((sub * 32 + lane) * C, T), t1 = min(t0 + C, T);
+    int cur = -1, head = -1;
+    double cr = 0.0, ci = 0.0;
+    double2 head_v = make_double2(0.0, 0.0);
 #pragma unroll 1
-    for (int q = sub * 32 + lane; q < n_out + stride; q += stride) {
-        const int blk = q / 64, pos = q % 64;
-        const int o = blk * 64 + ((pos < 32) ? pos : 95 - pos);  // pos 32..63 -> 63..32
-        if (o >= n_out) continue;
-        int n, m;
-        out_nm(o, n, m);
-        double ar = 0.0, ai = 0.0;
-#pragma unroll 1
-        for (int k = 0; k <= n; ++k) {
-            const int nn = n - k;
-            const int kr = k * k + k, kf = nn * nn + nn;
-            // |m + fs l| <= n - k and |l| <= k
-            const int l0 = (fs > 0) ? max(-k, -nn - m) : max(-k, m - nn);
-            const int l1 = (fs > 0) ? min(k, nn - m) : min(k, m + nn);
-            // two independent accumulator pairs (even / odd l)
-            double sr0 = 0.0, si0 = 0.0, sr1 = 0.0, si1 = 0.0;
-            int l = l0;
-            for (; l + 1 <= l1; l += 2) {
-                const double2 r0 = Rc[kr + l], f0 = Fc[kf + m + fs * l];
-                const double2 r1 = Rc[kr + l + 1], f1 = Fc[kf + m + fs * (l + 1)];
-                sr0 = fma(r0.x, f0.x, fma(-r0.y, f0.y, sr0));
-                si0 = fma(r0.x, f0.y, fma(r0.y, f0.x, si0));
-                sr1 = fma(r1.x, f1.x, fma(-r1.y, f1.y, sr1));
-                si1 = fma(r1.x, f1.y, fma(r1.y, f1.x, si1));
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t cd = __ldg(code + t);
+        const int o = (int)(cd >> 19);
+        if (o != cur) {
+            if (cur >= 0) {
+                if (head < 0) {
+                    head = cur;
+                    head_v = make_double2(cr, ci);
+                } else {
+                    row[cur] = make_double2(cr, ci);  // wholly inside this run
+                }
             }
-            if (l <= l1) {
-                const double2 r0 = Rc[kr + l], f0 = Fc[kf + m + fs * l];
-                sr0 = fma(r0.x, f0.x, fma(-r0.y, f0.y, sr0));
-                si0 = fma(r0.x, f0.y, fma(r0.y, f0.x, si0));
-            }
-            double sr = sr0 + sr1, si = si0 + si1;
-            if (fs > 0 && (k & 1)) {  // (-1)^k of the COEFF formula
-                sr = -sr;
-                si = -si;
-            }
-            ar += sr;
-            ai += si;
+            cur = o;
+            cr = ci = 0.0;
         }
-        row[o] = make_double2(ar, ai);
+        const double2 r = Rc[cd & 1023u], f = Fc[(cd >> 10) & 511u];
+        cr = fma(r.x, f.x, fma(-r.y, f.y, cr));
+        ci = fma(r.x, f.y, fma(r.y, f.x, ci));
+    }
+    if (head < 0) {
+        s_head_o[wib][lane] = cur;
+        s_head_v[wib][lane] = make_double2(cr, ci);
+        s_tail_o[wib][lane] = -1;
+    } else {
+        s_head_o[wib][lane] = head;
+        s_head_v[wib][lane] = head_v;
+        s_tail_o[wib][lane] = cur;
+        s_tail_v[wib][lane] = make_double2(cr, ci);
+    }
+    if (a.cta_per_source)
+        __syncthreads();
+    else
+        __syncwarp();
+    if (lane == 0 && (!a.cta_per_source || wib == 0)) {
+        int co = -1;
+        double2 cv = make_double2(0.0, 0.0);
+        const int w0 = a.cta_per_source ? 0 : wib, w1 = a.cta_per_source ? TR_WARPS : wib + 1;
+        for (int w = w0; w < w1; ++w)
+        for (int L = 0; L < 32; ++L) {
+            for (int side = 0; side < 2; ++side) {
+                const int o = side ? s_tail_o[w][L] : s_head_o[w][L];
+                if (o < 0) continue;
+                const double2 v = side ? s_tail_v[w][L] : s_head_v[w][L];
+                if (o == co) {
+                    cv.x += v.x;
+                    cv.y += v.y;
+                } else {
+                    if (co >= 0) row[co] = cv;
+                    co = o;
+                    cv = v;
+                }
+            }
+        }
+        if (co >= 0) row[co] = cv;
     }
 }
 
@@ -237,6 +320,7 @@ extern "C" q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const
     cudaError_t e = cudaSetDevice(plan->device);
     if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "cudaSetDevice");
     q2x::TransArgs a;
+    a.cta_per_source = 0;
     a.p = p;
     a.np = (p + 1) * (p + 1);
     a.n_out = (p + 1) * (p + 2) / 2;
@@ -254,18 +338,13 @@ extern "C" q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const
     if (st != Q2X_OK) return st;
     a.rows = static_cast<double2*>(plan->ws);
     if (n_src > 0) {
-        const size_t smem = (size_t)q2x::TR_WARPS * 2 * a.np * sizeof(double2);
+        const size_t smem = (size_t)q2x::TR_WARPS * 3 * q2x::TR_NP_MAX * sizeof(double2);
         e = cudaFuncSetAttribute(q2x::q2x_translate_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "cudaFuncSetAttribute");
-        // few sources (the top of a tree): split each translation over up to
-        // 8 warps so the level is not one warp's latency
-        const int64_t target = (int64_t)plan->num_sms * 8;
-        const int64_t want = std::max<int64_t>(1, std::min<int64_t>({8, target / n_src, (a.n_out + 31) / 32}));
-        a.wps_log2 = 0;
-        while ((2LL << a.wps_log2) <= want) ++a.wps_log2;
-        a.wps = 1 << a.wps_log2;
-        const int64_t warps = n_src * a.wps;
-        const int64_t grid = (warps + q2x::TR_WARPS - 1) / q2x::TR_WARPS;
+        // few sources (the top of a tree): a CTA per source, so a level is
+        // not the latency of one warp's FP64 stream
+        a.cta_per_source = (n_src * 4 <= (int64_t)plan->num_sms * 8) ? 1 : 0;
+        const int64_t grid = a.cta_per_source ? n_src : (n_src + q2x::TR_WARPS - 1) / q2x::TR_WARPS;
         q2x::q2x_translate_rows<<<(unsigned)grid, q2x::TR_WARPS * 32, smem, plan->stream>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "q2x_translate_rows launch");
