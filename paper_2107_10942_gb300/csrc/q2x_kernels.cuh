@@ -277,8 +277,7 @@ struct cf_nb {
 };
 __device__ __forceinline__ cf_nb cf_neighbours(cf a, cf b)
 {
-    // swap(a + b) with two scalar adds written straight into the swapped
-    // halves (no register moves)
+    // swap(a + b) as two scalar adds
     float ar, ai, br, bi;
     cf_parts(a, ar, ai);
     cf_parts(b, br, bi);
@@ -288,7 +287,14 @@ __device__ __forceinline__ cf cf_stencil_nb(const cf_nb& nb, cf c, cf src, cf X2
 {
     cf t = cf_fma(nZ2, c, src);
     t = cf_fma(X2, nb.d, t);
-    return cf_fma(YmY, nb.sw, t);
+    // the Y term as two scalar FMAs on the halves: its operand swap(a + b)
+    // is made of scalar sums, and forming it into a register pair for a
+    // paired FMA costs more than the extra instruction (measured)
+    float tr, ti, sr, si, yy, ny;
+    cf_parts(t, tr, ti);
+    cf_parts(nb.sw, sr, si);
+    cf_parts(YmY, yy, ny);
+    return cf_make(fmaf(yy, sr, tr), fmaf(ny, si, ti));
 }
 __device__ __forceinline__ cf cf_stencil(cf a, cf b, cf c, cf src, cf X2, cf YmY, cf nZ2)
 {
