@@ -251,13 +251,6 @@ __device__ __forceinline__ cf cf_fma(cf a, cf b, cf c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
     return r;
 }
-// (re, im) -> (-re, im), i.e. -conj
-__device__ __forceinline__ cf cf_negconj(cf a)
-{
-    cf r;
-    r.v = a.v ^ 0x80000000ull;
-    return r;
-}
 __device__ __forceinline__ cf cf_zero()
 {
     cf r;
@@ -268,10 +261,10 @@ __device__ __forceinline__ cf cf_zero()
 // One tilde-stencil update in packed form: with a = x^{m-1}, b = x^{m+1},
 // c = x^m of degree n-1 and xi = X + iY,
 //   -xi a + eta b - z c + src = X (b - a) + (Y, -Y) * swap(a + b) - z c + src.
-// For m = 0 pass a = -conj(b): then -xi a + eta b = 2 Re(eta b) (Eq. (rec11))
-// and the imaginary part comes out exactly zero.  The two neighbour
-// combinations are formed once per row entry and shared by every stencil
-// applied to it (the output level and its double layer).
+// (At m = 0, Eq. (rec11) gives the real value 2 Re(eta b) - z c + src, which
+// the degree loop computes in scalar form.)  The two neighbour combinations
+// are formed once per row entry and shared by every stencil applied to it
+// (the output level and its double layer).
 struct cf_nb {
     cf d, sw;  // b - a and swap(a + b)
 };
@@ -295,10 +288,6 @@ __device__ __forceinline__ cf cf_stencil_nb(const cf_nb& nb, cf c, cf src, cf X2
     cf_parts(nb.sw, sr, si);
     cf_parts(YmY, yy, ny);
     return cf_make(fmaf(yy, sr, tr), fmaf(ny, si, ti));
-}
-__device__ __forceinline__ cf cf_stencil(cf a, cf b, cf c, cf src, cf X2, cf YmY, cf nZ2)
-{
-    return cf_stencil_nb(cf_neighbours(a, b), c, src, X2, YmY, nZ2);
 }
 
 // column c -> (n, m), exact for c < 2^20
@@ -899,13 +888,24 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                         for (int k = 0; k < NL; ++k) {
                             const cf c = R[k][m];
                             const cf b = (m < P) ? R[k][m < P ? m + 1 : P] : cf_zero();
-                            const cf a = (m == 0) ? cf_negconj(b) : pa[k];
+                            // m = 0 (Eq. (rec11)): 2 Re(eta b) - z c + src, real; scalar
+                            float br0 = 0.f, bi0 = 0.f, cr0 = 0.f, ci0 = 0.f;
+                            if (m == 0) {
+                                cf_parts(b, br0, bi0);
+                                cf_parts(c, cr0, ci0);
+                            }
+                            const cf a = (m == 0) ? cf_zero() : pa[k];
                             const cf_nb nbk = cf_neighbours(a, b);
                             if (KIND == KIND_TRI && k == OUT && want1) {
                                 // double layer from the output level's row n-1
-                                cf dl = cf_stencil_nb(nbk, c, cf_zero(), XN2, YNm, nZN2);
                                 float dr, di;
-                                cf_parts(dl, dr, di);
+                                if (m == 0) {
+                                    dr = fmaf(2.f * XN, br0, fmaf(2.f * YN, bi0, -ZN * cr0));
+                                    di = 0.f;
+                                } else {
+                                    cf dl = cf_stencil_nb(nbk, c, cf_zero(), XN2, YNm, nZN2);
+                                    cf_parts(dl, dr, di);
+                                }
                                 if (st) {
                                     trow1[m * LD] = (m & 1) ? di : dr;
                                     if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
@@ -922,7 +922,14 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                                 src = cf_fma(s1p, nw[3], nw[2]);  // E^ + s1 i^
                             else
                                 src = nw[k > 0 ? k - 1 : 0];
-                            nw[k] = cf_stencil_nb(nbk, c, src, X2[k], YmY[k], nZ2[k]);
+                            if (m == 0) {
+                                float sr0, si0;
+                                cf_parts(src, sr0, si0);
+                                nw[k] = cf_make(fmaf(2.f * LX[k], br0, fmaf(2.f * LY[k], bi0, fmaf(-LZ[k], cr0, sr0))),
+                                                0.f);
+                            } else {
+                                nw[k] = cf_stencil_nb(nbk, c, src, X2[k], YmY[k], nZ2[k]);
+                            }
                             pa[k] = c;
                             R[k][m] = nw[k];
                         }
