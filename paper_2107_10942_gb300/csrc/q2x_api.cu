@@ -175,37 +175,37 @@ __global__ void rho_bits_to_double(const int* bits, double* rho, int64_t n)
     if (L < n) rho[L] = (double)__int_as_float(bits[L]);
 }
 
-// segmented sum of per-element rows: one warp per leaf, lanes over columns,
-// elements in index order (deterministic)
+// segmented sum of per-element rows: one warp per (leaf, group of 32
+// columns), one column per lane, eight rows in flight per step; every column
+// is summed in element order (deterministic, the same order as a plain loop)
 __global__ void leaf_reduce_kernel(const double* __restrict__ elem, int np, int64_t n_elem,
                                    int64_t n_leaves, const int64_t* __restrict__ off, double* coef,
                                    int accumulate)
 {
+    constexpr int U = 8;
     const int lane = threadIdx.x & 31;
-    const int64_t L = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int groups = (np + 31) >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t L = gw / groups;
     if (L >= n_leaves) return;
+    const int c = (int)(gw - L * groups) * 32 + lane;
+    if (c >= np) return;
     // clamped: a bad leaf_off is reported by check_leaf_off_kernel, never read past
     const int64_t e0 = min(max(off[L], (int64_t)0), n_elem);
     const int64_t e1 = min(max(off[L + 1], e0), n_elem);
-    for (int c0 = 0; c0 < np; c0 += 32 * 4) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int64_t e = e0; e < e1; ++e) {
-            const double* row = elem + e * np;
+    const double* col = elem + c;
+    double acc = 0.0;
+    int64_t e = e0;
+    for (; e + U <= e1; e += U) {
+        double v[U];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int c = c0 + k * 32 + lane;
-                if (c < np) acc[k] += __ldg(row + c);
-            }
-        }
+        for (int u = 0; u < U; ++u) v[u] = __ldg(col + (e + u) * np);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int c = c0 + k * 32 + lane;
-            if (c < np) {
-                double* d = coef + L * np + c;
-                *d = accumulate ? *d + acc[k] : acc[k];
-            }
-        }
+        for (int u = 0; u < U; ++u) acc += v[u];
     }
+    for (; e < e1; ++e) acc += __ldg(col + e * np);
+    double* d = coef + L * np + c;
+    *d = accumulate ? *d + acc : acc;
 }
 
 // --------------------------------------------------------------- dispatch
@@ -571,7 +571,8 @@ q2x_status q2x_leaf_reduce(q2x_plan_t plan, int64_t n_elem, int p, const double*
     check_leaf_off_kernel<<<(unsigned)((n_leaves + 1 + 255) / 256), 256, 0, plan->stream>>>(leaf_off, n_leaves, n_elem,
                                                                                            plan->d_err);
     const int warps = 8;
-    leaf_reduce_kernel<<<(unsigned)((n_leaves + warps - 1) / warps), warps * 32, 0, plan->stream>>>(
+    const int64_t units = n_leaves * (int64_t)((np + 31) / 32);
+    leaf_reduce_kernel<<<(unsigned)((units + warps - 1) / warps), warps * 32, 0, plan->stream>>>(
         elem, np, n_elem, n_leaves, leaf_off, coef, accumulate);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(plan, e, "leaf_reduce launch");
