@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -145,8 +146,7 @@ class ClockSampler:
     def __init__(self, uuid=None):
         self.proc = None
         self.uuid = uuid
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/q2x_clocks_%d.csv" % os.getpid()
+        self.path = os.path.join(tempfile.gettempdir(), "q2x_clocks_%d.csv" % os.getpid())
 
     def start(self):
         cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]

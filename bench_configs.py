@@ -140,8 +140,8 @@ def run_mixed_ball(args, dev):
         kinds[names[k]] = {key: torch.from_numpy(v).to(dev) for key, v in dd.items()}
     lc, lr, lp = (torch.from_numpy(m[k]).to(dev) for k in ("leaf_c", "leaf_rho", "leaf_p"))
     plan = q.Plan(m["p"], precision="fp32")
-    tile = q.q2x.autotuned_tile(plan, "mixed-ball-%d" % m["leaf_c"].shape[1], "gpurun_out/autotune.json"
-                                if __import__("os").path.isdir("gpurun_out") else "/tmp/q2x_autotune.json",
+    tile = q.q2x.autotuned_tile(plan, "mixed-ball-%d" % m["leaf_c"].shape[1],
+                                __import__("os").path.join(__import__("tempfile").gettempdir(), "q2x_autotune.json"),
                                 candidates=(128, 256, 512, 1024, 2048), reps=3, leaf_c=lc, leaf_rho=lr, leaf_p=lp,
                                 **kinds)
     b = q.q2x.Batch(plan, lc, lr, lp, tile_elems=tile, **kinds)
