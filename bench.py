@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="sphere-L7-linear",
                     choices=["sphere-L7-linear", "icosphere-L3", "sphere-L9-const", "mixed-ball",
-                             "sphere-L8-adjoint", "upward", "far-field", "galerkin", "biot-savart", "leaf-reduce"],
+                             "sphere-L8-adjoint", "upward", "far-field", "galerkin", "biot-savart", "leaf-reduce",
+                             "near-field"],
                     help="workload; the default is the headline configuration, the others are the "
                          "precision, ragged-batch and adjoint configurations")
     return ap.parse_args()

@@ -495,6 +495,59 @@ def run_leaf_reduce(args, dev):
            "errors_vs_oracle": {"max_abs_vs_sequential_sum": err, "sampled_leaves": 20}})
 
 
+# FP64 operations per (target, triangle) pair of the closed form as the
+# near-field kernel writes it: frame and height (about 35), three edges of
+# about 46 each, and each sqrt, division, log and atan2 counted as one
+NEARFIELD_OPS_PER_PAIR = 35 + 3 * 46 + 14 + 7 + 3 + 6
+
+
+def run_nearfield(args, dev):
+    import paper_2107_10942_gb300 as q
+    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS
+    from oracle import nearfield as onf
+    p = 12
+    prob = W.cfg_sphere_linear(level=7, depth=5, p=p)
+    vx, idx, off = prob["vxyz"], prob["idx"], prob["leaf_off"]
+    n_elem, nl = idx.shape[1], prob["leaf_c"].shape[1]
+    sig = prob["sigma"][idx].mean(axis=0)  # a constant density per triangle
+    tgt = np.ascontiguousarray(vx[:, idx].mean(axis=1))  # collocation points: the centroids
+    cnt = np.diff(off)
+    leaf_of = np.repeat(np.arange(nl), cnt)
+    tgt_off = np.concatenate([[0], np.cumsum(cnt[leaf_of])]).astype(np.int64)
+    # target t lists every triangle of its own leaf
+    first = off[leaf_of]
+    rep = np.repeat(np.arange(n_elem), cnt[leaf_of])
+    elem_idx = (first[rep] + (np.arange(tgt_off[-1]) - tgt_off[rep])).astype(np.int64)
+    pairs = int(tgt_off[-1])
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+         for k, v in dict(vxyz=vx, idx=idx, sigma=sig, tgt=tgt, tgt_off=tgt_off, elem_idx=elem_idx).items()}
+    out = torch.empty(n_elem, dtype=torch.float64, device=dev)
+    plan = q.Plan(p, precision="fp64")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    run = lambda: plan.nearfield("triangle", d["vxyz"], d["idx"], d["sigma"], d["tgt"], d["tgt_off"], d["elem_idx"],
+                                 out=out)
+    ms = _time(run, args.steps, args.warmup, flush, stream)
+    got = out.cpu().numpy()
+    plan.sync()
+    rng = np.random.default_rng(31)
+    pick = rng.choice(n_elem, 12, replace=False)
+    lists = [range(off[leaf_of[t]], off[leaf_of[t] + 1]) for t in pick]
+    ref = onf.potentials("triangle", vx, idx, sig, tgt[:, pick], lists)
+    err = float(np.max(np.abs(got[pick] - ref)) / np.max(np.abs(ref)))
+    ops = NEARFIELD_OPS_PER_PAIR * pairs
+    _emit({"metric": "near-field element potentials/s (exact triangle integrals, Sec. 4.1)",
+           "value": pairs / (ms * 1e-3), "unit": "target-element pairs/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "collocation at the centroids of the level-7 sphere's %d triangles, each against "
+                                  "every triangle of its depth-5 leaf: %d pairs, single layer" % (n_elem, pairs)},
+           "roofline": {"bound": "alu", "achieved": ops / (ms * 1e-3) / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
+                        "unit": "TFLOP/s", "frac": ops / (ms * 1e-3) / PEAK_FP64_FLOPS,
+                        "ops_per_pair": NEARFIELD_OPS_PER_PAIR,
+                        "note": "sqrt, division, log and atan2 count as one operation each: a lower bound"},
+           "errors_vs_oracle": {"graded_quadrature": err, "sampled_targets": len(pick)}})
+
+
 def to_dev(prob, dev):
     from paper_2107_10942_gb300.q2x import problem_to_device
     return problem_to_device({k: v for k, v in prob.items() if hasattr(v, "shape")}, dev)
@@ -507,5 +560,5 @@ def run(args):
     build.build()
     {"icosphere-L3": run_icosphere_l3, "sphere-L9-const": run_sphere_l9, "upward": run_upward,
      "far-field": run_farfield, "galerkin": run_galerkin, "biot-savart": run_biot_savart,
-     "leaf-reduce": run_leaf_reduce, "mixed-ball": run_mixed_ball,
+     "leaf-reduce": run_leaf_reduce, "near-field": run_nearfield, "mixed-ball": run_mixed_ball,
      "sphere-L8-adjoint": run_adjoint}[args.config](args, dev)

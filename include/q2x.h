@@ -335,6 +335,25 @@ q2x_status q2x_evaluate_curl(q2x_plan_t plan, int p, int64_t n_exp, const double
                              int64_t n_tgt, const double* tgt, const int64_t* tgt_off, const int64_t* exp_idx,
                              double* out3, int accumulate);
 
+/* Near field: exact potentials of constant-density elements at targets,
+ *   out[t] (+)= sum over the elements e listed for target t of
+ *               sigma[e] / (4 pi) * int_e 1/|r_t - y| dmu(y)          (layer 0)
+ *               sigma[e] / (4 pi) * int_e n.(r_t - y)/|r_t - y|^3 dS   (layer 1,
+ *               triangles: the double-layer kernel, a signed solid angle)
+ * by the closed forms of Sec. 4.1 (Eqs. (num1)-(num3) for segments, the
+ * edge-sum form for flat triangles, the divergence-theorem face sum of
+ * Eqs. (num7)-(num8) for tetrahedra).  kind 0 segment, 1 triangle, 2
+ * tetrahedron; vxyz, idx, sigma (per element) as q2x_segments/-triangles/
+ * -tetra; tgt double[3 * n_tgt] SoA; tgt_off int64[n_tgt + 1] CSR into the
+ * element list elem_idx (int64); out double[n_tgt].  Targets on an element
+ * are handled where the integral exists (vertices and edges of the element
+ * give finite values).  An element index out of range sets the device error
+ * word (bit 1).  FP64. */
+q2x_status q2x_nearfield(q2x_plan_t plan, int kind, int layer, int64_t n_elem, int64_t n_vert,
+                         const double* vxyz, const int32_t* idx, const double* sigma, int64_t n_tgt,
+                         const double* tgt, const int64_t* tgt_off, const int64_t* elem_idx, double* out,
+                         int accumulate);
+
 /* Receiver-side (Galerkin) integration over triangles: for every triangle e
  * of leaf L,
  *   out[e] = sum_c w[L][c] P_c(e),

@@ -306,6 +306,33 @@ class Plan:
                                       _ptr(tgt_off), _ptr(exp_idx), _ptr(out), int(bool(accumulate))), self._h)
         return out
 
+    def nearfield(self, kind, vxyz, idx, sigma, tgt, tgt_off=None, elem_idx=None, layer=0, out=None,
+                  accumulate=False):
+        """Exact potentials (1/4pi) sigma_e int_e G of the listed elements at
+        the targets (3, n_tgt); default: every target, every element
+        (q2x_nearfield).  kind: "segment" | "triangle" | "tetra"."""
+        k = {"segment": 0, "triangle": 1, "tetra": 2}[kind]
+        n_vert, n_elem = self._geom(vxyz, idx, k + 2)
+        _need(sigma, torch.float64, "sigma", (n_elem,))
+        _need(tgt, torch.float64, "tgt")
+        if tgt.dim() != 2 or tgt.shape[0] != 3:
+            raise ValueError("tgt must be (3, n_tgt)")
+        n_tgt = tgt.shape[1]
+        if tgt_off is None:
+            tgt_off = torch.arange(n_tgt + 1, dtype=torch.int64, device=tgt.device) * n_elem
+            elem_idx = torch.arange(n_elem, dtype=torch.int64, device=tgt.device).repeat(n_tgt)
+        _need(tgt_off, torch.int64, "tgt_off", (n_tgt + 1,))
+        _need(elem_idx, torch.int64, "elem_idx")
+        if out is None:
+            if accumulate:
+                raise ValueError("accumulate=True needs an output tensor")
+            out = torch.empty(n_tgt, dtype=torch.float64, device=tgt.device)
+        _need(out, torch.float64, "out", (n_tgt,))
+        check(lib().q2x_nearfield(self._h, k, int(layer), n_elem, n_vert, _ptr(vxyz), _ptr(idx), _ptr(sigma), n_tgt,
+                                  _ptr(tgt), _ptr(tgt_off), _ptr(elem_idx), _ptr(out), int(bool(accumulate))),
+              self._h)
+        return out
+
     def galerkin_triangles(self, vxyz, idx, weights, leaf_off, leaf_c, leaf_rho=None, sigma=None, layer=0,
                            out=None):
         """Per-triangle contraction sum_c weights[L][c] P_c(e) of each
