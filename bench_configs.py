@@ -495,10 +495,13 @@ def run_leaf_reduce(args, dev):
            "errors_vs_oracle": {"max_abs_vs_sequential_sum": err, "sampled_leaves": 20}})
 
 
-# FP64 operations per (target, triangle) pair of the closed form as the
-# near-field kernel writes it: frame and height (about 35), three edges of
-# about 46 each, and each sqrt, division, log and atan2 counted as one
-NEARFIELD_OPS_PER_PAIR = 35 + 3 * 46 + 14 + 7 + 3 + 6
+# FP64 operations per (target, triangle) pair as the near-field kernel
+# evaluates the closed form from a precomputed face frame: frame coordinates
+# and height (about 20), three vertex distances (9), three edges of about 17
+# (edge coordinates, the log's argument), the solid angle's denominator (13),
+# the sums (2), and each of the 3 sqrt, 3 divisions, 3 log1p and 1 atan2
+# counted as one
+NEARFIELD_OPS_PER_PAIR = 20 + 9 + 3 * 17 + 13 + 2 + 3 + 3 + 3 + 1
 
 
 def run_nearfield(args, dev):

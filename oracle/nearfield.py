@@ -24,8 +24,9 @@ by Gauss-Legendre quadrature in coordinates centred on the target, where the
 Panels are graded geometrically toward each near-singular point -- the
 target's projection (scale: its height h) and the foot on each edge (scale:
 the distance to the edge's line) -- so targets close to an element converge
-like distant ones.  A height at rounding level (16 ulps of |r - x1|) counts
-as zero, where the double layer takes its direct value 0.  None of the
+like distant ones.  A height at the rounding level of the coordinates (16
+ulps of |r|_1 + |x1|_1) counts as zero: the target is taken in the plane,
+where the double layer has its direct value 0.  None of the
 closed forms of Sec. 4.1 is used here.
 
 parity pins: ``tests/test_oracle_nearfield.py`` (textbook closed forms:
@@ -43,7 +44,7 @@ from . import gauss_legendre
 INV_4PI = 1.0 / (4.0 * np.pi)
 
 
-SNAP = 16.0 * np.finfo(np.float64).eps  # heights at rounding level count as zero
+SNAP = 16.0 * np.finfo(np.float64).eps  # heights below 16 ulps of the coordinates count as zero
 
 
 def _graded(lo, hi, at, delta, nq):
@@ -95,37 +96,41 @@ def _plane_fan(X, r, f, nq):
     if J == 0.0:
         return 0.0, 0.0, None
     n = nr / J
-    dr = r - X[0]
-    h = float(np.dot(n, dr))
-    if abs(h) <= SNAP * np.linalg.norm(dr):
+    h = float(np.dot(n, r - X[0]))
+    if abs(h) <= SNAP * (np.sum(np.abs(r)) + np.sum(np.abs(X[0]))):
         h = 0.0
-    r0 = r - h * n
     tot = 0.0
     for i in range(3):
         a, b = X[i], X[(i + 1) % 3]
         e = b - a
-        jac = float(np.dot(np.cross(a - r0, e), n))
+        A = (a - r) + h * n  # a - r0, r0 = r - h n the projection
+        jac = float(np.dot(np.cross(A, e), n))
         if jac == 0.0:
             continue
         L = np.linalg.norm(e)
-        vstar = float(np.clip(np.dot(r0 - a, e) / (L * L), 0.0, 1.0))
+        vstar = float(np.clip(-np.dot(A, e) / (L * L), 0.0, 1.0))
         dline = abs(jac) / L  # distance from r0 to the edge's line
         v, wv = _graded(0.0, 1.0, vstar, dline / L, nq)
-        qmax = max(np.linalg.norm(a - r0), np.linalg.norm(b - r0))
+        qmax = max(np.linalg.norm(A), np.linalg.norm(A + e))
         u, wu = _graded(0.0, 1.0, 0.0, abs(h) / qmax, nq)
         U, V = np.meshgrid(u, v, indexing="ij")
-        y = r0 + U[..., None] * ((a - r0) + V[..., None] * e)
-        tot += jac * np.sum(np.outer(wu, wv) * U * f(r, y, n))
+        # r - y = h n - u (a - r0 + v (b - a)), formed relative to r so that
+        # points closer to r than the coordinates' rounding stay distinct
+        d = h * n - U[..., None] * (A + V[..., None] * e)
+        tot += jac * np.sum(np.outer(wu, wv) * U * f(d, n))
     return tot, h, n
 
 
-def _single(r, y, n):
-    return 1.0 / np.linalg.norm(r - y, axis=-1)
+def _single(d, n):
+    return 1.0 / np.linalg.norm(d, axis=-1)
 
 
-def _double(r, y, n):
-    d = r - y
+def _double(d, n):
     return (d @ n) / np.linalg.norm(d, axis=-1) ** 3
+
+
+def _cone(d, n):
+    return -(d @ n) / np.linalg.norm(d, axis=-1)
 
 
 def _triangle(X, r, layer, nq):
@@ -145,7 +150,7 @@ def _tetra(X, r, nq):
         F = X[list(f)]
         if np.dot(np.cross(F[1] - F[0], F[2] - F[0]), F[0] - c) < 0.0:  # outward orientation
             F = F[[0, 2, 1]]
-        v, h, _ = _plane_fan(F, r, lambda rr, y, n: ((y - rr) @ n) / np.linalg.norm(rr - y, axis=-1), nq)
+        v, h, _ = _plane_fan(F, r, _cone, nq)
         tot += 0.5 * v
     return tot
 
