@@ -42,7 +42,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP64
 # element kernel on this workload, from the ncu capture summarised in the
 # profile named below (set to None whenever the kernel changes)
-TRAFFIC_FP64 = 9702144 + 40209664
+TRAFFIC_FP64 = 9732864 + 39978752
 TRAFFIC_SOURCE = "ncu --set full, profiles/q2x_elem_kernel_sphere-L7-linear-p12.md (bytes per launch)"
 
 

@@ -76,8 +76,11 @@ __device__ __forceinline__ double line_log(double sm, double sp, double Rm, doub
     const double num = L * (Sg + fabs(sg));
     const double a = (sg >= 0.0) ? Rm : Rp;
     const double s = (sg >= 0.0) ? sm : -sp;
-    const double arg = (s >= 0.0) ? num / (Sg * (a + s)) : num * (a - s) / (Sg * d02);
-    return log1p(arg);
+    // selects, not branches: lanes see an edge from either side
+    const bool ahead = s >= 0.0;
+    const double numer = ahead ? num : num * (a - s);
+    const double denom = Sg * (ahead ? a + s : d02);
+    return log1p(numer / denom);
 }
 
 // A flat face in its own frame: origin x1, in-plane axes u (along the first
