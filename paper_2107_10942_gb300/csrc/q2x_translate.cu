@@ -123,8 +123,8 @@ static __device__ const TermTab g_terms = make_terms();
 // -R(t)) in each warp's shared memory, then the contraction over the
 // flattened term list, each lane a contiguous run of terms (equal work per
 // lane).  Outputs wholly inside a lane's run are written by that lane; the
-// partial sums of the outputs at run boundaries are added in run order by
-// the first thread of the warp (or CTA).
+// partial sums of an output split across runs are added in run order by the
+// lane whose run holds its first part.
 __global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -247,27 +247,42 @@ __global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransA
         __syncthreads();
     else
         __syncwarp();
-    if (lane == 0 && (!a.cta_per_source || wib == 0)) {
-        int co = -1;
-        double2 cv = make_double2(0.0, 0.0);
-        const int w0 = a.cta_per_source ? 0 : wib, w1 = a.cta_per_source ? TR_WARPS : wib + 1;
-        for (int w = w0; w < w1; ++w)
-        for (int L = 0; L < 32; ++L) {
-            for (int side = 0; side < 2; ++side) {
-                const int o = side ? s_tail_o[w][L] : s_head_o[w][L];
-                if (o < 0) continue;
-                const double2 v = side ? s_tail_v[w][L] : s_head_v[w][L];
-                if (o == co) {
-                    cv.x += v.x;
-                    cv.y += v.y;
-                } else {
-                    if (co >= 0) row[co] = cv;
-                    co = o;
-                    cv = v;
-                }
+    // boundary partials, summed in run order by the run that holds each
+    // output's first partial (all runs at once; the same order of addition
+    // as one sequential pass over the runs)
+    const int nr = 32 * nsub;
+    const int j = sub * 32 + lane;
+    auto slot = [&](int R) { return a.cta_per_source ? (R >> 5) : wib; };
+    auto HO = [&](int R) { return s_head_o[slot(R)][R & 31]; };
+    auto TO = [&](int R) { return s_tail_o[slot(R)][R & 31]; };
+    auto HV = [&](int R) { return s_head_v[slot(R)][R & 31]; };
+    const int ho = HO(j);
+    if (ho >= 0) {
+        const int prev = (j == 0) ? -1 : (TO(j - 1) >= 0 ? TO(j - 1) : HO(j - 1));
+        if (ho != prev) {
+            double2 v = HV(j);
+            int r = j;
+            while (TO(r) < 0 && r + 1 < nr && HO(r + 1) == ho) {
+                ++r;
+                const double2 w = HV(r);
+                v.x += w.x;
+                v.y += w.y;
             }
+            row[ho] = v;
         }
-        if (co >= 0) row[co] = cv;
+    }
+    const int to = TO(j);
+    if (to >= 0) {
+        double2 v = s_tail_v[slot(j)][lane];
+        int r = j;
+        while (r + 1 < nr && HO(r + 1) == to) {
+            ++r;
+            const double2 w = HV(r);
+            v.x += w.x;
+            v.y += w.y;
+            if (TO(r) >= 0) break;
+        }
+        row[to] = v;
     }
 }
 
