@@ -311,8 +311,10 @@ q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const double* sr
  *   coef     double[n_exp * (p+1)^2] packed (device); exp_c double[3 * n_exp] SoA
  *   tgt      double[3 * n_tgt] SoA target points (device)
  *   tgt_off  int64[n_tgt + 1] CSR into exp_idx (device); exp_idx int64 list of
- *            expansion indices (device, non-NULL); an index out of range sets
- *            the device error word (bit 1) and is skipped, a bad range sets bit 8
+ *            expansion indices (device; may be NULL when every list is
+ *            empty); an index out of range sets the device error word (bit 1)
+ *            and is skipped, a bad range (or a non-empty list with exp_idx
+ *            NULL) sets bit 8 and the target gets 0
  *   out      double[n_tgt] (device), overwritten or added to (accumulate = 1)
  * FP64 arithmetic in both precisions of the plan; S_n^m by the
  * associated-Legendre recurrences in Cartesian form (Eqs. (bas1)-(bas2)). */
@@ -345,10 +347,19 @@ q2x_status q2x_evaluate_curl(q2x_plan_t plan, int p, int64_t n_exp, const double
  * Eqs. (num7)-(num8) for tetrahedra).  kind 0 segment, 1 triangle, 2
  * tetrahedron; vxyz, idx, sigma (per element) as q2x_segments/-triangles/
  * -tetra; tgt double[3 * n_tgt] SoA; tgt_off int64[n_tgt + 1] CSR into the
- * element list elem_idx (int64); out double[n_tgt].  Targets on an element
- * are handled where the integral exists (vertices and edges of the element
- * give finite values).  An element index out of range sets the device error
- * word (bit 1).  FP64. */
+ * element list elem_idx (int64; may be NULL when every list is empty); out
+ * double[n_tgt], overwritten or added to (accumulate = 1); all device
+ * arrays.  Targets on an element are handled where the integral exists
+ * (vertices and edges of a triangle, and any point of a tetrahedron, give
+ * finite values; a target inside a segment gives inf).  A target within
+ * rounding of a triangle's plane is taken in it, where the double layer
+ * has its direct value 0.  An element or vertex index out of range sets
+ * the device error word (bit 1) and the element is skipped; a bad range
+ * (or a non-empty list with elem_idx NULL) sets bit 8 and the target gets
+ * 0.  Errors: Q2X_ERR_UNSUPPORTED for layer 1 with kind != 1, Q2X_ERR_ARG
+ * for bad kinds, sizes or NULL arrays.  Launches one frame kernel (kinds 1,
+ * 2; the face frames live in the plan's workspace) and one target kernel on
+ * the plan's stream.  FP64. */
 q2x_status q2x_nearfield(q2x_plan_t plan, int kind, int layer, int64_t n_elem, int64_t n_vert,
                          const double* vxyz, const int32_t* idx, const double* sigma, int64_t n_tgt,
                          const double* tgt, const int64_t* tgt_off, const int64_t* elem_idx, double* out,

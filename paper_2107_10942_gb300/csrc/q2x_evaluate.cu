@@ -11,8 +11,10 @@
 // by the associated-Legendre recurrences in Cartesian form:
 //   T_m^m = (-1)^m (2m-1)!! (x + iy)^m,  T_{m+1}^m = (2m+1) z T_m^m,
 //   (n - m) T_n^m = (2n-1) z T_{n-1}^m - (n+m-1) r^2 T_{n-2}^m.
-// One thread per (target, list entry); the order loop is outer, so a thread
-// holds two T values and needs no table.  FP64.
+// Since T_n^m = P_n T_m^m with a real sequence P_n, each order's column is
+// summed as Re(i^{-m} T_m^m sum_n F_n^m U_n) with U_n = (n-m)! r^{-2n-1} P_n
+// from a division-free real recurrence (see eval_one).  One thread per
+// target, looping over the target's expansion list (CSR).  FP64.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -34,90 +36,74 @@ struct EvalArgs {
     unsigned* err;
 };
 
-// k! (exact as doubles for k <= 20) and 1/k, k = 0..20
-struct FactTab {
-    double v[Q2X_P_MAX + 1];
-    double inv[Q2X_P_MAX + 1];
+// Recurrence constants of the scaled column sequence below: a_n = 2n - 1
+// and c_{n,m} = (n + m - 1)(n - m - 1), read warp-uniformly.
+struct EvalTab {
+    double a[Q2X_P_MAX + 1];
+    double c[Q2X_P_MAX + 1][Q2X_P_MAX + 1];  // [n][m]
 };
-constexpr FactTab make_fact_tab()
+constexpr EvalTab make_eval_tab()
 {
-    FactTab t{};
-    double f = 1.0;
-    for (int k = 0; k <= Q2X_P_MAX; ++k) {
-        if (k > 0) f *= k;
-        t.v[k] = f;
-        t.inv[k] = k > 0 ? 1.0 / k : 0.0;
+    EvalTab t{};
+    for (int n = 0; n <= Q2X_P_MAX; ++n) {
+        t.a[n] = 2.0 * n - 1.0;
+        for (int m = 0; m <= Q2X_P_MAX; ++m) t.c[n][m] = (double)((n + m - 1) * (n - m - 1));
     }
     return t;
 }
-static __constant__ FactTab c_fact = make_fact_tab();
+static __constant__ EvalTab c_eval = make_eval_tab();
 
 // Far-field value of one expansion at offset (x, y, z) from its centre.
+// With T_n^m the Cartesian associated-Legendre polynomials (Eqs. (bas1)-
+// (bas2)), T_n^m = P_n T_m^m for a real sequence P_n (P_m = 1, P_{m-1} = 0)
+// that obeys the same three-term recurrence in n, so that
+//   S_n^m = i^{-m} (n-m)! r^{-2n-1} T_n^m = i^{-m} T_m^m U_n,
+//   U_n = (n-m)! r^{-2n-1} P_n,
+//   U_n = a_n (z / r^2) U_{n-1} - c_{n,m} U_{n-2} / r^2,  U_m = r^{-2m-1},
+// and the order-m column sums to Re(i^{-m} T_m^m sum_n F_n^m U_n): per term
+// a real three-term step and two FMAs, no division.  For MOMENT
+// coefficients, F_n^m = (1/4pi)(-1)^{n+m} conj(M_n^m); the sign (-1)^{n-m}
+// is absorbed by running the recurrence with -z.
 __device__ double eval_one(const double* __restrict__ F, int p, int norm, double x, double y, double z)
 {
     const double r2 = x * x + y * y + z * z;
     if (!(r2 > 0.0)) return 0.0;  // at the centre the series does not apply
-    const double ir2 = 1.0 / r2;
-    const double ir = sqrt(ir2);
+    const double rho2 = 1.0 / r2;
+    const double zr = (norm != 0 ? -z : z) * rho2;
+    double rp = sqrt(rho2);       // r^{-2m-1}
+    double tmr = 1.0, tmi = 0.0;  // T_m^m = (-1)^m (2m-1)!! (x + iy)^m
     double total = 0.0;
-    // (x + iy)^m (-1)^m (2m-1)!! = T_m^m, updated per order
-    double tmr = 1.0, tmi = 0.0;
 #pragma unroll 1
     for (int m = 0; m <= p; ++m) {
         if (m > 0) {  // T_m^m = -(2m-1) (x + iy) T_{m-1}^{m-1}
-            const double f = -(double)(2 * m - 1);
+            const double f = -c_eval.a[m];
             const double nr = f * (x * tmr - y * tmi);
             const double ni = f * (x * tmi + y * tmr);
             tmr = nr;
             tmi = ni;
+            rp *= rho2;
         }
-        // i^{-m} rotation of the order-m column
-        double rot_r, rot_i;
-        switch (m & 3) {
-            case 0: rot_r = 1.0; rot_i = 0.0; break;
-            case 1: rot_r = 0.0; rot_i = -1.0; break;
-            case 2: rot_r = -1.0; rot_i = 0.0; break;
-            default: rot_r = 0.0; rot_i = 1.0; break;
-        }
-        double t2r = 0.0, t2i = 0.0;  // T_{n-2}^m
-        double t1r = tmr, t1i = tmi;  // T_{n-1}^m, starting at n = m
-        // r^{-2n-1} at n = m
-        double irp = ir;
-        for (int j = 0; j < m; ++j) irp *= ir2;
-        double col = 0.0;
+        const int km = m * m + m;
+        double u1 = rp, u2 = 0.0;  // U_n, U_{n-1}
+        double ar = __ldg(F + km + m) * u1;
+        double ai = m ? __ldg(F + km - m) * u1 : 0.0;
 #pragma unroll 1
-        for (int n = m; n <= p; ++n) {
-            double tr, ti;
-            if (n == m) {
-                tr = t1r;
-                ti = t1i;
-            } else {
-                const double a = (double)(2 * n - 1), b = (double)(n + m - 1), inv = c_fact.inv[n - m];
-                tr = (a * z * t1r - b * r2 * t2r) * inv;
-                ti = (a * z * t1i - b * r2 * t2i) * inv;
-                t2r = t1r;
-                t2i = t1i;
-                t1r = tr;
-                t1i = ti;
-                irp *= ir2;
-            }
-            // S_n^m = i^{-m} (n-m)! r^{-2n-1} T_n^m
-            const double sc = c_fact.v[n - m] * irp;
-            const double sr = sc * (rot_r * tr - rot_i * ti);
-            const double si = sc * (rot_r * ti + rot_i * tr);
-            // coefficient of (n, m): COEFF F_n^m; MOMENT (1/4pi)(-1)^n M_n^{-m} = ... (-1)^{n+m} conj(M_n^m)
+        for (int n = m + 1; n <= p; ++n) {
+            const double u = fma(c_eval.a[n] * zr, u1, -(c_eval.c[n][m] * rho2) * u2);
+            u2 = u1;
+            u1 = u;
             const int k0 = n * n + n;
-            double cr = __ldg(F + k0 + m);
-            double ci = m ? __ldg(F + k0 - m) : 0.0;
-            if (norm != 0) {
-                const double sg = (((n + m) & 1) ? -1.0 : 1.0) * 0.079577471545947667884;
-                cr = sg * cr;
-                ci = -sg * ci;
-            }
-            const double v = cr * sr - ci * si;  // Re(coef * S)
-            col += (m == 0) ? v : 2.0 * v;
+            ar = fma(__ldg(F + k0 + m), u, ar);
+            if (m) ai = fma(__ldg(F + k0 - m), u, ai);
         }
-        total += col;
+        if (norm != 0) {  // conj, 1/4pi
+            ar *= 0.079577471545947667884;
+            ai *= -0.079577471545947667884;
+        }
+        const double wr = tmr * ar - tmi * ai, wi = tmr * ai + tmi * ar;
+        // Re(i^{-m} w)
+        const double col = ((m & 3) == 0) ? wr : ((m & 3) == 1) ? wi : ((m & 3) == 2) ? -wr : -wi;
+        total += m ? 2.0 * col : col;
     }
     return total;
 }
@@ -127,7 +113,7 @@ __global__ void q2x_evaluate_kernel(const EvalArgs a)
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.n_tgt) return;
     int64_t j0 = __ldg(a.tgt_off + t), j1 = __ldg(a.tgt_off + t + 1);
-    if (j0 < 0 || j1 < j0) {
+    if (j0 < 0 || j1 < j0 || (j1 > j0 && a.exp_idx == nullptr)) {  // an empty list set may pass NULL
         atomicOr(a.err, 8u);
         j0 = j1 = 0;
     }
@@ -162,71 +148,71 @@ __device__ __forceinline__ D4 operator*(D4 a, D4 b)
     return D4{a.v * b.v, fma(a.v, b.x, a.x * b.v), fma(a.v, b.y, a.y * b.v), fma(a.v, b.z, a.z * b.v)};
 }
 
+__device__ __forceinline__ D4 fma4(double s, D4 a, D4 acc)
+{
+    return D4{fma(s, a.v, acc.v), fma(s, a.x, acc.x), fma(s, a.y, acc.y), fma(s, a.z, acc.z)};
+}
+
 // Gradients of the three component series A_k(x) = sum F^(k)_n^m S_n^m(x - c)
 // at offset (x, y, z): g[k] += grad A_k.  F3 holds the three packed rows of
-// one expansion, `stride` apart (COEFF norm).
+// one expansion, `stride` apart (COEFF norm).  The same column form as
+// eval_one, S_n^m = i^{-m} T_m^m U_n, carried in value-and-gradient numbers.
 __device__ void grad_one(const double* __restrict__ F3, int64_t stride, int p, double x, double y, double z,
                          double g[3][3])
 {
     const double r2v = x * x + y * y + z * z;
     if (!(r2v > 0.0)) return;
     const D4 X{x, 1.0, 0.0, 0.0}, Y{y, 0.0, 1.0, 0.0}, Z{z, 0.0, 0.0, 1.0};
-    const D4 r2 = X * X + Y * Y + Z * Z;
-    // 1/r^2 and 1/r with their gradients: d(1/r2) = -dr2 / r2^2, d(r^-1) = -(1/2) r^-3 dr2
+    // 1/r^2 and 1/r with their gradients: d(1/r^2) = -2 x / r^4, d(1/r) = -x / r^3
     const double ir2v = 1.0 / r2v, irv = sqrt(ir2v);
-    const D4 ir2{ir2v, -r2.x * ir2v * ir2v, -r2.y * ir2v * ir2v, -r2.z * ir2v * ir2v};
-    const double c = -0.5 * irv * ir2v;
-    const D4 ir{irv, c * r2.x, c * r2.y, c * r2.z};
-    D4 tmr = d4(1.0), tmi = d4(0.0);
+    const double c2 = -2.0 * ir2v * ir2v, c1 = -irv * ir2v;
+    const D4 rho2{ir2v, c2 * x, c2 * y, c2 * z};
+    const D4 zr = Z * rho2;
+    D4 rp{irv, c1 * x, c1 * y, c1 * z};  // r^{-2m-1}
+    D4 tmr = d4(1.0), tmi = d4(0.0);    // T_m^m
 #pragma unroll 1
     for (int m = 0; m <= p; ++m) {
         if (m > 0) {
-            const double f = -(double)(2 * m - 1);
+            const double f = -c_eval.a[m];
             const D4 nr = f * (X * tmr - Y * tmi);
             const D4 ni = f * (X * tmi + Y * tmr);
             tmr = nr;
             tmi = ni;
+            rp = rp * rho2;
         }
-        double rot_r, rot_i;
-        switch (m & 3) {
-            case 0: rot_r = 1.0; rot_i = 0.0; break;
-            case 1: rot_r = 0.0; rot_i = -1.0; break;
-            case 2: rot_r = -1.0; rot_i = 0.0; break;
-            default: rot_r = 0.0; rot_i = 1.0; break;
+        const int km = m * m + m;
+        D4 u1 = rp, u2 = d4(0.0);
+        D4 ar[3], ai[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            ar[k] = __ldg(F3 + k * stride + km + m) * u1;
+            ai[k] = m ? __ldg(F3 + k * stride + km - m) * u1 : d4(0.0);
         }
-        D4 t2r = d4(0.0), t2i = d4(0.0);
-        D4 t1r = tmr, t1i = tmi;
-        D4 irp = ir;
-        for (int j = 0; j < m; ++j) irp = irp * ir2;
-        const double w = m ? 2.0 : 1.0;
 #pragma unroll 1
-        for (int n = m; n <= p; ++n) {
-            D4 tr, ti;
-            if (n == m) {
-                tr = t1r;
-                ti = t1i;
-            } else {
-                const double a = (double)(2 * n - 1), b = (double)(n + m - 1), inv = c_fact.inv[n - m];
-                tr = inv * (a * (Z * t1r) - b * (r2 * t2r));
-                ti = inv * (a * (Z * t1i) - b * (r2 * t2i));
-                t2r = t1r;
-                t2i = t1i;
-                t1r = tr;
-                t1i = ti;
-                irp = irp * ir2;
-            }
-            const D4 sc = c_fact.v[n - m] * irp;
-            const D4 sr = sc * (rot_r * tr - rot_i * ti);
-            const D4 si = sc * (rot_r * ti + rot_i * tr);
+        for (int n = m + 1; n <= p; ++n) {
+            const D4 u = c_eval.a[n] * (zr * u1) - c_eval.c[n][m] * (rho2 * u2);
+            u2 = u1;
+            u1 = u;
             const int k0 = n * n + n;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const double cr = __ldg(F3 + k * stride + k0 + m);
-                const double ci = m ? __ldg(F3 + k * stride + k0 - m) : 0.0;
-                g[k][0] += w * (cr * sr.x - ci * si.x);
-                g[k][1] += w * (cr * sr.y - ci * si.y);
-                g[k][2] += w * (cr * sr.z - ci * si.z);
+                ar[k] = fma4(__ldg(F3 + k * stride + k0 + m), u, ar[k]);
+                if (m) ai[k] = fma4(__ldg(F3 + k * stride + k0 - m), u, ai[k]);
             }
+        }
+        const double w = m ? 2.0 : 1.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            // Re(i^{-m} T_m^m A): only the part the order's rotation selects
+            D4 col;
+            if ((m & 1) == 0)
+                col = tmr * ar[k] - tmi * ai[k];  // Re(T A)
+            else
+                col = tmr * ai[k] + tmi * ar[k];  // Im(T A)
+            const double sg = ((m & 3) >= 2) ? -w : w;
+            g[k][0] = fma(sg, col.x, g[k][0]);
+            g[k][1] = fma(sg, col.y, g[k][1]);
+            g[k][2] = fma(sg, col.z, g[k][2]);
         }
     }
 }
@@ -237,7 +223,7 @@ __global__ void q2x_evaluate_curl_kernel(const EvalArgs a)
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.n_tgt) return;
     int64_t j0 = __ldg(a.tgt_off + t), j1 = __ldg(a.tgt_off + t + 1);
-    if (j0 < 0 || j1 < j0) {
+    if (j0 < 0 || j1 < j0 || (j1 > j0 && a.exp_idx == nullptr)) {  // an empty list set may pass NULL
         atomicOr(a.err, 8u);
         j0 = j1 = 0;
     }
@@ -274,7 +260,7 @@ extern "C" q2x_status q2x_evaluate_curl(q2x_plan_t plan, int p, int64_t n_exp, c
     if (n_exp < 0 || n_tgt < 0) return q2x_fail(plan, Q2X_ERR_ARG, "negative size");
     if (accumulate != 0 && accumulate != 1) return q2x_fail(plan, Q2X_ERR_ARG, "accumulate must be 0 or 1");
     if (n_tgt == 0) return Q2X_OK;
-    if (!tgt || !tgt_off || !exp_idx || !out3) return q2x_fail(plan, Q2X_ERR_ARG, "NULL target array");
+    if (!tgt || !tgt_off || !out3) return q2x_fail(plan, Q2X_ERR_ARG, "NULL target array");
     if (n_exp > 0 && (!coef3 || !exp_c)) return q2x_fail(plan, Q2X_ERR_ARG, "NULL expansion array");
     cudaError_t e = cudaSetDevice(plan->device);
     if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "cudaSetDevice");
@@ -308,7 +294,7 @@ extern "C" q2x_status q2x_evaluate(q2x_plan_t plan, int p, int64_t n_exp, const 
     if (n_exp < 0 || n_tgt < 0) return q2x_fail(plan, Q2X_ERR_ARG, "negative size");
     if (accumulate != 0 && accumulate != 1) return q2x_fail(plan, Q2X_ERR_ARG, "accumulate must be 0 or 1");
     if (n_tgt == 0) return Q2X_OK;
-    if (!tgt || !tgt_off || !exp_idx || !out) return q2x_fail(plan, Q2X_ERR_ARG, "NULL target array");
+    if (!tgt || !tgt_off || !out) return q2x_fail(plan, Q2X_ERR_ARG, "NULL target array");
     if (n_exp > 0 && (!coef || !exp_c)) return q2x_fail(plan, Q2X_ERR_ARG, "NULL expansion array");
     cudaError_t e = cudaSetDevice(plan->device);
     if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "cudaSetDevice");

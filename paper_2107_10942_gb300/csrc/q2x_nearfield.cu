@@ -219,7 +219,7 @@ __global__ void q2x_nearfield_kernel(const NearArgs a, const Face* __restrict__ 
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.n_tgt) return;
     int64_t j0 = __ldg(a.tgt_off + t), j1 = __ldg(a.tgt_off + t + 1);
-    if (j0 < 0 || j1 < j0) {
+    if (j0 < 0 || j1 < j0 || (j1 > j0 && a.elem_idx == nullptr)) {  // an empty list set may pass NULL
         atomicOr(a.err, 8u);
         j0 = j1 = 0;
     }
@@ -283,7 +283,7 @@ extern "C" q2x_status q2x_nearfield(q2x_plan_t plan, int kind, int layer, int64_
     if (n_tgt == 0) return Q2X_OK;
     if (n_elem > ((int64_t)1 << 36) || n_tgt > ((int64_t)1 << 36))
         return q2x_fail(plan, Q2X_ERR_ARG, "n_elem or n_tgt too large");
-    if (!tgt || !tgt_off || !elem_idx || !out) return q2x_fail(plan, Q2X_ERR_ARG, "NULL target array");
+    if (!tgt || !tgt_off || !out) return q2x_fail(plan, Q2X_ERR_ARG, "NULL target array");
     if (n_elem > 0 && (!vxyz || !idx || !sigma || n_vert <= 0))
         return q2x_fail(plan, Q2X_ERR_ARG, "NULL element array or no vertices");
     cudaError_t e = cudaSetDevice(plan->device);

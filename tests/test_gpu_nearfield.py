@@ -139,3 +139,30 @@ def test_nearfield_accumulate_and_bad_index(q2x):
     assert out[1].item() == 0.0 and out[0].item() != 0.0
     with pytest.raises(q2x.Q2XError):
         plan.nearfield("segment", d["vxyz"], d["idx"], d["sigma"], tgt, layer=1)
+
+
+def test_nearfield_empty_lists(q2x):
+    """Targets with empty lists get 0 (or keep their value when accumulating);
+    no targets and no elements are valid calls."""
+    prob = random_problem("triangle", [4], seed=27, p=4)
+    d = {k: T(v) for k, v in prob.items() if hasattr(v, "shape")}
+    tgt = T(np.array([[1.0, 2.0, 3.0], [0.5, -0.5, 0.0], [2.0, 0.0, 1.0]]))
+    plan = q2x.Plan(4, precision="fp64")
+    off = torch.tensor([0, 0, 2, 2], dtype=torch.int64, device="cuda")
+    el = torch.tensor([1, 3], dtype=torch.int64, device="cuda")
+    got = plan.nearfield("triangle", d["vxyz"], d["idx"], d["sigma"], tgt, off, el)
+    ref = plan.nearfield("triangle", d["vxyz"], d["idx"], d["sigma"], tgt[:, 1:2].contiguous(),
+                         torch.tensor([0, 2], dtype=torch.int64, device="cuda"), el)
+    base = torch.full((3,), 7.0, dtype=torch.float64, device="cuda")
+    acc = plan.nearfield("triangle", d["vxyz"], d["idx"], d["sigma"], tgt, off, el, out=base.clone(),
+                         accumulate=True)
+    # every list empty: the index array may be empty (a NULL pointer)
+    zero = torch.zeros(4, dtype=torch.int64, device="cuda")
+    none = torch.empty(0, dtype=torch.int64, device="cuda")
+    empty = plan.nearfield("triangle", d["vxyz"], d["idx"], d["sigma"], tgt, zero, none)
+    no_tgt = plan.nearfield("triangle", d["vxyz"], d["idx"], d["sigma"], torch.empty((3, 0), dtype=torch.float64,
+                                                                                     device="cuda"))
+    plan.sync()
+    assert got[0].item() == 0.0 and got[2].item() == 0.0 and got[1].item() == ref[0].item() != 0.0
+    assert acc[0].item() == 7.0 and acc[2].item() == 7.0 and acc[1].item() == 7.0 + ref[0].item()
+    assert torch.all(empty == 0) and no_tgt.numel() == 0
