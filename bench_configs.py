@@ -498,7 +498,9 @@ def run_leaf_reduce(args, dev):
            "config": {"workload": "%d per-element rows of (p+1)^2 = %d FP64 into the level-7 sphere's %d leaves"
                                   % (n_elem, np_, nl)},
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                        "peak_source": src, "bytes_per_launch": bytes_},
+                        "peak_source": src, "bytes_per_launch": bytes_,
+                        "traffic": 444171776 + 7598336,
+                        "traffic_source": "ncu --set full, profiles/leaf_reduce_kernel_sphere-L7-p12.md"},
            "errors_vs_oracle": {"max_abs_vs_sequential_sum": err, "sampled_leaves": 20}})
 
 
