@@ -222,11 +222,17 @@ def run_adjoint(args, dev):
     rel_v = float(np.max(np.abs(gv32 - gv64)) / np.max(np.abs(gv64)))
     rel_s = float(np.max(np.abs(gs32 - gs64)) / np.max(np.abs(gs64)))
     per_step = n_elem * (p + 1) ** 2
+    from paper_2107_10942_gb300.roofline import PEAK_FP32_FLOPS, element_flops, vjp_flops
+    flops = float(element_flops("triangle", "const", ("single",), p) + vjp_flops(p)) * n_elem
     _emit({"metric": METRIC + " (forward + adjoint)", "value": per_step / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "dtype": "f32-mixed forward, f32 per element + f64 accumulation backward", "data": "synthetic",
            "config": {"workload": "sphere-L8-adjoint: %d triangles, depth 6, p=12, single layer, "
                                   "loss = sum(G * coef), G ~ N(0,1)" % n_elem},
+           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP32_FLOPS / 1e12,
+                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP32_FLOPS,
+                        "flops_per_element": flops / n_elem,
+                        "note": "whole step (forward kernel + adjoint kernels + autograd glue) against the FP32 peak"},
            "errors_vs_fp64_adjoint": {"grad_vertices": rel_v, "grad_sigma": rel_s}})
 
 

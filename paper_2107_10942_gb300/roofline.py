@@ -54,3 +54,14 @@ def element_flops(kind: str, density: str = "const", layers=("single",), p: int 
         f += L
     f += len(layers) * (p + 1) ** 2
     return f
+
+
+def vjp_flops(p: int = 12) -> int:
+    """Flops per triangle of the single-layer adjoint (q2x_tri_vjp_kernel):
+    seven chain levels (q, j, i and E, Iw for the barycentric weights of
+    vertices 2 and 3), and per (n, m >= 0) ten contractions with the folded
+    weights (S_U and the three directions of the three vertices; 4 flops
+    each) plus the e_x / e_y neighbour combinations of the three weighted
+    rows (8 adds each)."""
+    entries = sum(n + 1 for n in range(p + 1))
+    return 7 * level_flops(p) + 10 * 4 * entries + 3 * 8 * entries
