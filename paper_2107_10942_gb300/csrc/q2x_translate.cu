@@ -213,7 +213,9 @@ __global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransA
     int cur = -1, head = -1;
     double cr = 0.0, ci = 0.0;
     double2 head_v = make_double2(0.0, 0.0);
-#pragma unroll 1
+    // unrolled so that the term codes of several iterations are in flight
+    // at once (the small levels at the top of a tree are latency-bound)
+#pragma unroll 4
     for (int t = t0; t < t1; ++t) {
         const uint32_t cd = __ldg(code + t);
         const int o = (int)(cd >> 19);
@@ -300,6 +302,7 @@ __global__ void q2x_translate_combine(const TransArgs a)
     double* out = a.dst_coef + d * (int64_t)a.np;
     for (int o = lane; o < a.n_out; o += 32) {
         double2 v = make_double2(0.0, 0.0);
+#pragma unroll 4
         for (int64_t s = s0; s < s1; ++s) {
             const double2 r = a.rows[s * (int64_t)a.n_out + o];
             v.x += r.x;

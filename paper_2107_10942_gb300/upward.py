@@ -129,6 +129,33 @@ class Upward:
         codes = _morton(np.rint((lc[:, sel] - lo) / h - 0.5).astype(np.int64), dmax)
         return sel[np.argsort(codes, kind="stable")].astype(np.int64)
 
+    def capture(self, leaf_coef):
+        """Record the pass on the buffer `leaf_coef` as one CUDA graph (one
+        eager run first sizes the plan's workspace).  `replay()` then re-runs
+        the whole pass -- every level's kernels -- with one launch from the
+        host, reading whatever `leaf_coef` holds at that time; it returns the
+        same list of per-level tensors as `run`."""
+        self.run(leaf_coef)
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        old = self.plan._stream
+        self.plan.set_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        try:
+            with torch.cuda.graph(graph, stream=side):
+                outs = self.run(leaf_coef)
+        finally:
+            self.plan.set_stream(old)
+        self._graph, self._graph_outs = graph, outs
+        return outs
+
+    def replay(self):
+        """Replay the captured pass on the current stream."""
+        if getattr(self, "_graph", None) is None:
+            raise RuntimeError("capture() the pass first")
+        self._graph.replay()
+        return self._graph_outs
+
     def run(self, leaf_coef):
         src = leaf_coef if self.identity else leaf_coef.index_select(0, self.deep_idx)
         src_c = self.leaf_c if self.identity else self.leaf_c.index_select(1, self.deep_idx)

@@ -176,3 +176,35 @@ def test_upward_pass_adaptive_mixed_ball(q2x, orc):
     for box in range(c1.shape[1]):
         inside = np.nonzero(np.all(np.abs(m["leaf_c"] - c1[:, box:box + 1]) < 0.5, axis=0))[0]
         assert norm_err(lvl1[box:box + 1], quad(c1[:, box], inside), p, [radius(c1[:, box], inside)], 0) <= 1e-12
+
+
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_upward_graph_replay_bitwise(q2x, adaptive):
+    """The captured pass replays to the same bits as the eager pass, and
+    follows new leaf values written into the captured input buffer."""
+    from paper_2107_10942_gb300.q2x import problem_to_device
+    from paper_2107_10942_gb300.upward import Upward
+    p = 8
+    if adaptive:
+        m = W.cfg_mixed_ball(n_fil=20, n_steps=60, tri_level=3, n_tri=800, tet_spacing=0.25, n_tet=600,
+                             max_per_leaf=120, max_depth=8, p_lo=p, p_hi=p, seed=12)
+        leaf_c, lo, size, depth = m["leaf_c"], -1.0, 2.0, m["leaf_depth"]
+    else:
+        prob = W.cfg_sphere_linear(level=4, depth=3, p=p)
+        leaf_c, lo, size, depth = prob["leaf_c"], -1.125, 2.25, 3
+    nl = leaf_c.shape[1]
+    plan = q2x.Plan(p, precision="fp64")
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    leaf = torch.randn((nl, (p + 1) ** 2), dtype=torch.float64, device="cuda", generator=gen)
+    up = Upward(plan, leaf_c, lo, size, depth)
+    eager = [t.clone() for t in up.run(leaf)]
+    up.capture(leaf)
+    got = up.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(eager, got))
+    leaf.copy_(torch.randn(leaf.shape, dtype=torch.float64, device="cuda", generator=gen))
+    eager2 = [t.clone() for t in up.run(leaf)]
+    got2 = [t.clone() for t in up.replay()]
+    plan.sync()
+    assert all(torch.equal(a, b) for a, b in zip(eager2, got2))
+    assert not torch.equal(eager[-1], eager2[-1])
