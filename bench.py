@@ -44,6 +44,9 @@ L2_FLUSH_BYTES = 256 << 20
 # profile named below (set to None whenever the kernel changes)
 TRAFFIC_FP64 = 9732864 + 39978752
 TRAFFIC_SOURCE = "ncu --set full, profiles/q2x_elem_kernel_sphere-L7-linear-p12.md (bytes per launch)"
+# FP64 flops the same capture counted as executed per launch: 2 x DFMA + DADD + DMUL
+# thread instructions (168.70 + 79.73 + 11.38 per elapsed cycle over 6.674 M cycles)
+EXECUTED_FLOPS_FP64 = (2 * 168.701704 + 79.728916 + 11.382976) * 6673646.0
 
 
 def parse():
@@ -403,6 +406,9 @@ def main():
                      "traffic_source": TRAFFIC_SOURCE,
                      "kernel": "q2x_elem_kernel<double,12,TRI,LINEAR>", "kernel_ms": r64["kernel_ms"],
                      "flops_per_launch": flops_elem * n_elem,
+                     "executed": {"flops_per_launch": EXECUTED_FLOPS_FP64,
+                                  "frac": EXECUTED_FLOPS_FP64 / (r64["kernel_ms"] * 1e-3) / PEAK_FP64_FLOPS,
+                                  "source": "ncu DFMA/DADD/DMUL counts, " + TRAFFIC_SOURCE},
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz (recipe FP64 1.25 TF)"},
         "fp32_mixed": {"value": total_moments / (r32["ms"] * 1e-3), "ms_per_step": r32["ms"],
                        "speedup_vs_fp64": r64["ms"] / r32["ms"],
