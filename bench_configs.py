@@ -326,6 +326,11 @@ def run_upward(args, dev):
                             "%.2f s" % (prob["idx"].shape[1], dt), "kind": "oracle", "cores": orc.max_threads()}})
 
 
+# FP64 flops per evaluation ncu counted as executed at p = 12:
+# (2 x 104.19 + 13.57 + 137.94) per elapsed cycle x 2.858 M cycles / 1,048,576
+EVAL_EXECUTED_FLOPS = (2 * 104.187417 + 13.573713 + 137.938271) * 2858268.0 / 1048576
+
+
 def eval_flops(p):
     """Flops of one far-field evaluation (q2x_evaluate): per (n, m >= 0)
     term a three-term step (3 multiplies, 1 FMA) and two FMAs = 9 flops; per
@@ -370,7 +375,11 @@ def run_farfield(args, dev):
                                   "on the radius-3 sphere" % n_tgt},
            "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
                         "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP64_FLOPS,
-                        "flops_per_evaluation": eval_flops(p)},
+                        "flops_per_evaluation": eval_flops(p),
+                        "executed": {"flops_per_evaluation": EVAL_EXECUTED_FLOPS,
+                                     "frac": EVAL_EXECUTED_FLOPS * n_tgt / (ms * 1e-3) / PEAK_FP64_FLOPS,
+                                     "source": "ncu DFMA/DADD/DMUL counts, "
+                                               "profiles/q2x_evaluate_kernel_far-field-p12.md"}},
            "errors_vs_oracle": {"series": err, "sampled_targets": 64}})
 
 
@@ -519,6 +528,10 @@ def run_leaf_reduce(args, dev):
 # the sums (2), and each of the 3 sqrt, 3 divisions, 3 log1p and 1 atan2
 # counted as one
 NEARFIELD_OPS_PER_PAIR = 20 + 9 + 3 * 17 + 13 + 2 + 3 + 3 + 3 + 1
+# FP64 flops per pair ncu counted as executed (2 x DFMA + DADD + DMUL thread
+# instructions, library sequences of sqrt, division, log1p and atan2 included):
+# (2 x 92.31 + 33.24 + 37.07) per elapsed cycle x 59.66 M cycles / 39.54 M pairs
+NEARFIELD_EXECUTED_FLOPS_PER_PAIR = (2 * 92.309745 + 33.237194 + 37.074234) * 59656234.0 / 39541618
 
 
 def run_nearfield(args, dev):
@@ -564,7 +577,12 @@ def run_nearfield(args, dev):
            "roofline": {"bound": "alu", "achieved": ops / (ms * 1e-3) / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
                         "unit": "TFLOP/s", "frac": ops / (ms * 1e-3) / PEAK_FP64_FLOPS,
                         "ops_per_pair": NEARFIELD_OPS_PER_PAIR,
-                        "note": "sqrt, division, log and atan2 count as one operation each: a lower bound"},
+                        "note": "sqrt, division, log and atan2 count as one operation each: a lower bound",
+                        "executed": {"flops_per_pair": NEARFIELD_EXECUTED_FLOPS_PER_PAIR,
+                                     "frac": NEARFIELD_EXECUTED_FLOPS_PER_PAIR * pairs / (ms * 1e-3)
+                                     / PEAK_FP64_FLOPS,
+                                     "source": "ncu DFMA/DADD/DMUL counts, "
+                                               "profiles/q2x_nearfield_kernel_sphere-L7-collocation.md"}},
            "errors_vs_oracle": {"graded_quadrature": err, "sampled_targets": len(pick)}})
 
 
