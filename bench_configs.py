@@ -425,7 +425,7 @@ def run_galerkin(args, dev):
 
 def run_biot_savart(args, dev):
     import paper_2107_10942_gb300 as q
-    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS, element_flops
+    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS, level_flops
     from paper_2107_10942_gb300.upward import Upward
     p = 12
     m = W.cfg_mixed_ball()
@@ -456,13 +456,14 @@ def run_biot_savart(args, dev):
                     flush, stream)
     plan.sync()
     per_step = 3 * n_elem * (p + 1) ** 2
-    flops = 3 * element_flops("segment", "const", ("single",), p) * n_elem
+    # one recursion (the segment chain's two levels) and three weighted sums (one FMA per column each)
+    flops = (2 * level_flops(p) + 3 * 2 * (p + 1) ** 2) * n_elem
     _emit({"metric": "vector line-density Q2X element-moments/s (three components, Eq. st3)",
            "value": per_step / (ms_q2x * 1e-3), "unit": "element-moments/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_q2x, "higher_is_better": True, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": "the mixed ball's %d filament segments with vortex currents along them, %d "
-                                  "adaptive leaves, p=12 (one segment pass per component)" % (n_elem,
+                                  "adaptive leaves, p=12 (one recursion pass for the three components)" % (n_elem,
                                                                                            m["leaf_c"].shape[1])},
            "roofline": {"bound": "alu", "achieved": flops / (ms_q2x * 1e-3) / 1e12,
                         "peak": PEAK_FP64_FLOPS / 1e12, "unit": "TFLOP/s",

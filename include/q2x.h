@@ -396,6 +396,39 @@ q2x_status q2x_leaf_reduce(q2x_plan_t plan, int64_t n_elem, int p, const double*
                            int64_t n_leaves, const int64_t* leaf_off, double* coef,
                            int accumulate);
 
+/* Vector line density (Eq. (st3)): the coefficients of the three components
+ * of a current constant per segment, current double[3 * n_elem] (component
+ * j at current + j * n_elem), into coef3 double[3 * n_leaves * (p_max+1)^2]
+ * (component j's block at coef3 + j * n_leaves * (p_max+1)^2), otherwise the
+ * arguments of q2x_segments (leaf_off required).  The moments are geometric
+ * and each component multiplies them, so the recursion runs once per
+ * element: a per-element pass stores each element's unfinished moments about
+ * its leaf's centre (chunks of at most 1 GiB of rows, stream-ordered
+ * allocation on the plan's stream), then one weighted segmented sum per
+ * (leaf, column) forms the three components and finishes them.  Same
+ * results as three q2x_segments calls with the components as densities, up
+ * to rounding; deterministic. */
+q2x_status q2x_segments_vector(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const double* vxyz,
+                               const int32_t* idx, const double* current, int64_t n_leaves,
+                               const int64_t* leaf_off, const double* leaf_c, const double* leaf_rho,
+                               const int32_t* leaf_p, double* coef3, int accumulate);
+
+/* Weighted segmented sums of per-element rows, n_w components at once
+ * (1 <= n_w <= 4):
+ *   coef[j][L] (+)= sum_{e in leaf L} w[j][e] * elem[e],   j < n_w,
+ * component j's weights at w + j * w_stride (n_elem doubles each) and its
+ * output block (n_leaves * (p+1)^2 doubles) at coef + j * coef_stride.  With
+ * the unit-density moments of each element as elem, these are the
+ * coefficients of a vector density (Eq. (st3): the moments are geometric and
+ * each component multiplies them), so the three components of a line
+ * current share one recursion pass.  FP64, deterministic (each sum in
+ * element order, one FMA per element); leaf_off as above (required; a bad
+ * range sets bit 8 of the device error word and is clamped). */
+q2x_status q2x_leaf_reduce_weighted(q2x_plan_t plan, int64_t n_elem, int p, const double* elem, int n_w,
+                                    const double* w, int64_t w_stride, int64_t n_leaves,
+                                    const int64_t* leaf_off, double* coef, int64_t coef_stride,
+                                    int accumulate);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,6 +37,8 @@ _SIGNATURES = {
     "q2x_translate": [_p, _i, _i64, _p, _p, _i64, _p, _p, _p, _i],
     "q2x_evaluate": [_p, _i, _i64, _p, _p, _i64, _p, _p, _p, _p, _i],
     "q2x_evaluate_curl": [_p, _i, _i64, _p, _p, _i64, _p, _p, _p, _p, _i],
+    "q2x_segments_vector": [_p, _i64, _i64, _p, _p, _p, _i64, _p, _p, _p, _p, _p, _i],
+    "q2x_leaf_reduce_weighted": [_p, _i64, _i, _p, _i, _p, _i64, _i64, _p, _p, _i64, _i],
     "q2x_nearfield": [_p, _i, _i, _i64, _i64, _p, _p, _p, _i64, _p, _p, _p, _p, _i],
     "q2x_galerkin_triangles": [_p, _i64, _i64, _p, _p, _p, _i64, _p, _p, _p, _i, _p, _p],
     "q2x_triangles_single_vjp": [_p, _i64, _i64, _p, _p, _p, _i64, _p, _p, _p, _p, _p, _p, _p],

@@ -208,13 +208,138 @@ __global__ void leaf_reduce_kernel(const double* __restrict__ elem, int np, int6
     *d = accumulate ? *d + acc : acc;
 }
 
+// The same walk with NW weighted sums per column: acc_j = fma(w_j[e], v, acc_j)
+// in element order.
+template <int NW>
+__global__ void leaf_reduce_weighted_kernel(const double* __restrict__ elem, int np, int64_t n_elem,
+                                            const double* __restrict__ w, int64_t w_stride, int64_t n_leaves,
+                                            const int64_t* __restrict__ off, double* coef, int64_t coef_stride,
+                                            int accumulate)
+{
+    constexpr int U = 8;
+    const int lane = threadIdx.x & 31;
+    const int groups = (np + 31) >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t L = gw / groups;
+    if (L >= n_leaves) return;
+    const int c = (int)(gw - L * groups) * 32 + lane;
+    if (c >= np) return;
+    const int64_t e0 = min(max(off[L], (int64_t)0), n_elem);
+    const int64_t e1 = min(max(off[L + 1], e0), n_elem);
+    const double* col = elem + c;
+    double acc[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) acc[j] = 0.0;
+    int64_t e = e0;
+    for (; e + U <= e1; e += U) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = __ldg(col + (e + u) * np);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int j = 0; j < NW; ++j) acc[j] = fma(__ldg(w + j * w_stride + e + u), v[u], acc[j]);
+    }
+    for (; e < e1; ++e) {
+        const double v = __ldg(col + e * np);
+#pragma unroll
+        for (int j = 0; j < NW; ++j) acc[j] = fma(__ldg(w + j * w_stride + e), v, acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        double* d = coef + j * coef_stride + L * np + c;
+        *d = accumulate ? *d + acc[j] : acc[j];
+    }
+}
+
+// Per-element copies of the leaf data for the per-element pass over the
+// elements [e0, e0 + m) of a vector density: each element's leaf centre,
+// scale and degree, its vertex indices, and a unit density.
+__global__ void vector_gather_kernel(const int64_t* __restrict__ off, int64_t n_leaves,
+                                     const double* __restrict__ leaf_c, const double* __restrict__ rho,
+                                     const int32_t* __restrict__ leaf_p, const int32_t* __restrict__ idx,
+                                     int64_t n_elem, int64_t e0, int64_t m, double* ec, double* er, int32_t* ep,
+                                     int32_t* idxc, double* ones)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t e = e0 + i;
+    const int64_t L = q2x::leaf_search(off, 0, n_leaves - 1, e);
+    ec[i] = __ldg(leaf_c + L);
+    ec[m + i] = __ldg(leaf_c + n_leaves + L);
+    ec[2 * m + i] = __ldg(leaf_c + 2 * n_leaves + L);
+    if (er) er[i] = __ldg(rho + L);
+    if (ep) ep[i] = __ldg(leaf_p + L);
+    idxc[i] = __ldg(idx + e);
+    idxc[m + i] = __ldg(idx + n_elem + e);
+    ones[i] = 1.0;
+}
+
+// The three components of a vector density from the unfinished per-element
+// rows of the elements [e0, e1): per (leaf, column), the weighted sums
+// sum_e cur[j][e] rows[e] in element order, finished once per leaf (the
+// finish is linear: 1/(n+d)!, the packing sign, 1/4pi, the leaf's scale).
+__global__ void vector_reduce_kernel(const double* __restrict__ rows, int np, int64_t e0, int64_t e1,
+                                     int64_t n_elem, const double* __restrict__ cur, int64_t n_leaves,
+                                     const int64_t* __restrict__ off, const double* __restrict__ rho,
+                                     const int32_t* __restrict__ leaf_p, int p_max, int norm, int d, int shift_n0,
+                                     double* coef, int accumulate)
+{
+    constexpr int U = 8;
+    const int lane = threadIdx.x & 31;
+    const int groups = (np + 31) >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t L = gw / groups;
+    if (L >= n_leaves) return;
+    const int c = (int)(gw - L * groups) * 32 + lane;
+    if (c >= np) return;
+    const int64_t lo = min(max(max(off[L], (int64_t)0), e0), e1);
+    const int64_t hi = min(max(min(off[L + 1], n_elem), lo), e1);
+    if (lo == hi && accumulate) return;  // nothing of this leaf in the chunk
+    const double* col = rows + c;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    int64_t e = lo;
+    for (; e + U <= hi; e += U) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = __ldg(col + (e + u - e0) * np);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            a0 = fma(__ldg(cur + e + u), v[u], a0);
+            a1 = fma(__ldg(cur + n_elem + e + u), v[u], a1);
+            a2 = fma(__ldg(cur + 2 * n_elem + e + u), v[u], a2);
+        }
+    }
+    for (; e < hi; ++e) {
+        const double v = __ldg(col + (e - e0) * np);
+        a0 = fma(__ldg(cur + e), v, a0);
+        a1 = fma(__ldg(cur + n_elem + e), v, a1);
+        a2 = fma(__ldg(cur + 2 * n_elem + e), v, a2);
+    }
+    const int desc = q2x::col_desc(c);
+    int pl = p_max;
+    if (leaf_p) {
+        pl = __ldg(leaf_p + L);
+        if (pl < 0 || pl > p_max) pl = -1;
+    }
+    const int s = rho ? q2x::scale_exponent(__ldg(rho + L)) : 0;
+    const bool keep = (desc & 31) <= pl;
+    const double acc[3] = {a0, a1, a2};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const double v = keep ? q2x::finish_desc(acc[j], norm, desc, d, shift_n0, s) : 0.0;
+        double* dst = coef + (j * n_leaves + L) * (int64_t)np + c;
+        *dst = accumulate ? *dst + v : v;
+    }
+}
+
 // --------------------------------------------------------------- dispatch
 
 q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int64_t n_vert,
                         const double* vxyz, const int32_t* idx, const double* sigma,
                         int64_t n_leaves, const int64_t* leaf_off, const double* leaf_c,
                         const double* leaf_rho, const int32_t* leaf_p, double* coef0,
-                        double* coef1, int accumulate)
+                        double* coef1, int accumulate, int raw = 0)
 {
     if (!plan) return fail(nullptr, Q2X_ERR_ARG, "plan is NULL");
     if (n_elem < 0 || n_vert < 0 || n_leaves < 0)
@@ -321,6 +446,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     a.n_ranges = n_ranges;
     a.slots = ws;
     a.err = plan->d_err;
+    a.raw = raw;
 
     const int grid = (int)((n_ranges + q2x::WARPS_PER_CTA - 1) / q2x::WARPS_PER_CTA);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -576,6 +702,143 @@ q2x_status q2x_leaf_reduce(q2x_plan_t plan, int64_t n_elem, int p, const double*
         elem, np, n_elem, n_leaves, leaf_off, coef, accumulate);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(plan, e, "leaf_reduce launch");
+    plan->launches += 2;
+    return Q2X_OK;
+}
+
+q2x_status q2x_segments_vector(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const double* vxyz,
+                               const int32_t* idx, const double* current, int64_t n_leaves,
+                               const int64_t* leaf_off, const double* leaf_c, const double* leaf_rho,
+                               const int32_t* leaf_p, double* coef3, int accumulate)
+{
+    if (!plan) return fail(nullptr, Q2X_ERR_ARG, "plan is NULL");
+    if (n_elem < 0 || n_vert < 0 || n_leaves < 0) return fail(plan, Q2X_ERR_ARG, "negative size");
+    if (accumulate != 0 && accumulate != 1) return fail(plan, Q2X_ERR_ARG, "accumulate must be 0 or 1");
+    if (!leaf_off || !coef3) return fail(plan, Q2X_ERR_ARG, "leaf_off and coef3 must be non-NULL");
+    if (n_elem > 0 && (!vxyz || !idx || !current || !leaf_c || n_vert <= 0 || n_leaves <= 0))
+        return fail(plan, Q2X_ERR_ARG, "NULL array or empty mesh");
+    if (n_elem > ((int64_t)1 << 40)) return fail(plan, Q2X_ERR_ARG, "n_elem too large");
+    if (n_leaves == 0) return Q2X_OK;
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "cudaSetDevice");
+    const int np = (plan->p_max + 1) * (plan->p_max + 1);
+    if (n_elem == 0) {
+        if (!accumulate) {
+            e = cudaMemsetAsync(coef3, 0, sizeof(double) * 3 * (size_t)n_leaves * np, plan->stream);
+            if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMemsetAsync");
+        }
+        return Q2X_OK;
+    }
+    check_leaf_off_kernel<<<(unsigned)((n_leaves + 1 + 255) / 256), 256, 0, plan->stream>>>(leaf_off, n_leaves, n_elem,
+                                                                                           plan->d_err);
+    plan->launches += 1;
+    // elements in chunks whose unfinished rows take at most 1 GiB
+    const int64_t m_max = std::min<int64_t>(n_elem, std::max<int64_t>(1024, ((int64_t)1 << 30) / (8 * np)));
+    const bool need_rho = plan->prec == 1 && leaf_rho == nullptr;  // FP32 needs the leaf scale
+    const size_t b_rows = align_up(sizeof(double) * (size_t)m_max * np, 256);
+    const size_t b_ec = align_up(sizeof(double) * 3 * (size_t)m_max, 256);
+    const size_t b_er = align_up(sizeof(double) * (size_t)m_max, 256);
+    const size_t b_ep = align_up(sizeof(int32_t) * (size_t)m_max, 256);
+    const size_t b_idx = align_up(sizeof(int32_t) * 2 * (size_t)m_max, 256);
+    const size_t b_one = align_up(sizeof(double) * (size_t)m_max, 256);
+    const size_t b_rho = need_rho ? align_up(sizeof(double) * (size_t)n_leaves, 256) : 0;
+    const size_t b_bits = need_rho ? align_up(sizeof(int) * (size_t)n_leaves, 256) : 0;
+    unsigned char* tmp = nullptr;
+    e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), b_rows + b_ec + b_er + b_ep + b_idx + b_one + b_rho + b_bits,
+                        plan->stream);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMallocAsync (vector rows)");
+    double* rows = reinterpret_cast<double*>(tmp);
+    double* ec = reinterpret_cast<double*>(tmp + b_rows);
+    double* er = reinterpret_cast<double*>(tmp + b_rows + b_ec);
+    int32_t* ep = reinterpret_cast<int32_t*>(tmp + b_rows + b_ec + b_er);
+    int32_t* idxc = reinterpret_cast<int32_t*>(tmp + b_rows + b_ec + b_er + b_ep);
+    double* ones = reinterpret_cast<double*>(tmp + b_rows + b_ec + b_er + b_ep + b_idx);
+    const double* rho = leaf_rho;
+    q2x_status st = Q2X_OK;
+    if (need_rho) {
+        double* r = reinterpret_cast<double*>(tmp + b_rows + b_ec + b_er + b_ep + b_idx + b_one);
+        int* bits = reinterpret_cast<int*>(tmp + b_rows + b_ec + b_er + b_ep + b_idx + b_one + b_rho);
+        e = cudaMemsetAsync(bits, 0, sizeof(int) * (size_t)n_leaves, plan->stream);
+        if (e == cudaSuccess) {
+            leaf_rho_kernel<<<(unsigned)((n_elem + 255) / 256), 256, 0, plan->stream>>>(
+                n_elem, n_vert, 2, vxyz, vxyz + n_vert, vxyz + 2 * n_vert, idx, n_leaves, leaf_off, leaf_c, bits);
+            rho_bits_to_double<<<(unsigned)((n_leaves + 255) / 256), 256, 0, plan->stream>>>(bits, r, n_leaves);
+            plan->launches += 2;
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) st = cuda_fail(plan, e, "leaf scale");
+        rho = r;
+    }
+    using C = q2x::Chain<q2x::KIND_SEG, q2x::DENS_CONST>;
+    const int64_t units = n_leaves * (int64_t)((np + 31) / 32);
+    for (int64_t e0 = 0; st == Q2X_OK && e0 < n_elem; e0 += m_max) {
+        const int64_t m = std::min(m_max, n_elem - e0);
+        vector_gather_kernel<<<(unsigned)((m + 255) / 256), 256, 0, plan->stream>>>(
+            leaf_off, n_leaves, leaf_c, rho, leaf_p, idx, n_elem, e0, m, ec, rho ? er : nullptr,
+            leaf_p ? ep : nullptr, idxc, ones);
+        plan->launches += 1;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            st = cuda_fail(plan, e, "vector gather launch");
+            break;
+        }
+        st = run_elements(plan, q2x::KIND_SEG, Q2X_DENSITY_CONST, m, n_vert, vxyz, idxc, ones, m, nullptr, ec,
+                          rho ? er : nullptr, leaf_p ? ep : nullptr, rows, nullptr, 0, /*raw=*/1);
+        if (st != Q2X_OK) break;
+        vector_reduce_kernel<<<(unsigned)((units + 7) / 8), 256, 0, plan->stream>>>(
+            rows, np, e0, e0 + m, n_elem, current, n_leaves, leaf_off, rho, leaf_p, plan->p_max, plan->norm,
+            C::D_OUT, q2x::KIND_SEG + 1, coef3, e0 == 0 ? accumulate : 1);
+        plan->launches += 1;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_fail(plan, e, "vector reduce launch");
+    }
+    e = cudaFreeAsync(tmp, plan->stream);
+    if (st == Q2X_OK && e != cudaSuccess) st = cuda_fail(plan, e, "cudaFreeAsync");
+    return st;
+}
+
+q2x_status q2x_leaf_reduce_weighted(q2x_plan_t plan, int64_t n_elem, int p, const double* elem, int n_w,
+                                    const double* w, int64_t w_stride, int64_t n_leaves,
+                                    const int64_t* leaf_off, double* coef, int64_t coef_stride,
+                                    int accumulate)
+{
+    if (!plan) return fail(nullptr, Q2X_ERR_ARG, "plan is NULL");
+    if (p < 0 || p > plan->p_max) return fail(plan, Q2X_ERR_RANGE, "p %d outside 0..%d", p, plan->p_max);
+    if (n_w < 1 || n_w > 4) return fail(plan, Q2X_ERR_ARG, "n_w %d outside 1..4", n_w);
+    if (n_elem < 0 || n_leaves < 0 || w_stride < 0 || coef_stride < 0) return fail(plan, Q2X_ERR_ARG, "negative size");
+    if (!leaf_off || !coef || (n_elem > 0 && (!elem || !w))) return fail(plan, Q2X_ERR_ARG, "NULL pointer");
+    if (accumulate != 0 && accumulate != 1) return fail(plan, Q2X_ERR_ARG, "accumulate must be 0 or 1");
+    const int np = (p + 1) * (p + 1);
+    if (n_w > 1 && (w_stride < n_elem || coef_stride < n_leaves * (int64_t)np))
+        return fail(plan, Q2X_ERR_ARG, "component strides overlap");
+    if (n_leaves == 0) return Q2X_OK;
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e != cudaSuccess) return cuda_fail(plan, e, "cudaSetDevice");
+    check_leaf_off_kernel<<<(unsigned)((n_leaves + 1 + 255) / 256), 256, 0, plan->stream>>>(leaf_off, n_leaves, n_elem,
+                                                                                           plan->d_err);
+    const int warps = 8;
+    const int64_t units = n_leaves * (int64_t)((np + 31) / 32);
+    const unsigned grid = (unsigned)((units + warps - 1) / warps);
+    switch (n_w) {
+        case 1:
+            leaf_reduce_weighted_kernel<1><<<grid, warps * 32, 0, plan->stream>>>(
+                elem, np, n_elem, w, w_stride, n_leaves, leaf_off, coef, coef_stride, accumulate);
+            break;
+        case 2:
+            leaf_reduce_weighted_kernel<2><<<grid, warps * 32, 0, plan->stream>>>(
+                elem, np, n_elem, w, w_stride, n_leaves, leaf_off, coef, coef_stride, accumulate);
+            break;
+        case 3:
+            leaf_reduce_weighted_kernel<3><<<grid, warps * 32, 0, plan->stream>>>(
+                elem, np, n_elem, w, w_stride, n_leaves, leaf_off, coef, coef_stride, accumulate);
+            break;
+        default:
+            leaf_reduce_weighted_kernel<4><<<grid, warps * 32, 0, plan->stream>>>(
+                elem, np, n_elem, w, w_stride, n_leaves, leaf_off, coef, coef_stride, accumulate);
+            break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(plan, e, "leaf_reduce_weighted launch");
     plan->launches += 2;
     return Q2X_OK;
 }

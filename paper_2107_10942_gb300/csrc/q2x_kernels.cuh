@@ -104,6 +104,7 @@ struct ElemArgs {
     int64_t n_ranges;
     void* slots;              // [n_ranges][2 slots][2 layers][np_max] accumulators
     unsigned* err;
+    int raw = 0;              // per-element mode: store the hat sums unfinished
 };
 
 // ------------------------------------------------------------- constants
@@ -492,8 +493,9 @@ __device__ __forceinline__ void flush_value(const ElemArgs& a, const RangeCtx& r
         const int desc = col_desc(c);
         double v = 0.0;
         if ((desc & 31) < ((info >> 1) & 63))  // n <= p_leaf
-            v = finish_desc(acc, a.norm, desc, ly ? rc.d_out1 : rc.d_out0, ly ? rc.shift_n01 : rc.shift_n00,
-                            info >> 7);
+            v = a.raw ? (double)acc
+                      : finish_desc(acc, a.norm, desc, ly ? rc.d_out1 : rc.d_out0, ly ? rc.shift_n01 : rc.shift_n00,
+                                    info >> 7);
         double* dst = a.coef[ly] + (int64_t)L * a.np_max + c;
         if (a.accumulate)
             *dst += v;
@@ -566,7 +568,8 @@ __device__ __forceinline__ void reduce_chunk(const ElemArgs& a, const RangeCtx& 
     const int nlay = (want0 ? 1 : 0) + (want1 ? 1 : 0);
     const int total = nlay * ncols;
     if (per_elem) {
-#pragma unroll 1
+        // rows unrolled so that several rows' stores are in flight
+#pragma unroll 4
         for (int r = 0; r < nrows; ++r) {
             const long long L = rowleaf[r];
             const int info = rowinfo[r];

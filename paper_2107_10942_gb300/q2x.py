@@ -5,6 +5,7 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
 import torch
 
 from ._lib import check, lib
@@ -265,17 +266,55 @@ class Plan:
         return out
 
 
-    def segments_vector(self, vxyz, idx, current, leaf_off, leaf_c, leaf_rho=None, leaf_p=None):
+    def leaf_reduce_weighted(self, elem, p, leaf_off, weights, coef=None, accumulate=False):
+        """coef[j][L] (+)= sum_{e in leaf L} weights[j][e] elem[e] for the n_w
+        rows of weights (n_w <= 4), in element order (q2x_leaf_reduce_weighted).
+        weights (n_w, n_elem) and coef (n_w, n_leaves, (p+1)^2) may be views
+        whose rows are strided (e.g. a column range of a larger array)."""
+        _need(elem, torch.float64, "elem")
+        _need(leaf_off, torch.int64, "leaf_off")
+        nc = n_coef(p)
+        if elem.dim() != 2 or elem.shape[1] != nc:
+            raise ValueError("elem must be (n_elem, (p+1)^2)")
+        n_elem, n_leaves = elem.shape[0], leaf_off.shape[0] - 1
+        if not (isinstance(weights, torch.Tensor) and weights.is_cuda and weights.dtype == torch.float64
+                and weights.dim() == 2 and weights.shape[1] == n_elem and 1 <= weights.shape[0] <= 4
+                and (weights.stride(1) == 1 or n_elem <= 1)):
+            raise ValueError("weights must be a CUDA float64 (n_w <= 4, n_elem) array with unit column stride")
+        n_w = weights.shape[0]
+        if coef is None:
+            if accumulate:
+                raise ValueError("accumulate=True needs an output tensor")
+            coef = torch.empty((n_w, n_leaves, nc), dtype=torch.float64, device=elem.device)
+        if not (isinstance(coef, torch.Tensor) and coef.is_cuda and coef.dtype == torch.float64
+                and tuple(coef.shape) == (n_w, n_leaves, nc) and coef.stride(2) == 1 and coef.stride(1) == nc):
+            raise ValueError("coef must be a CUDA float64 (n_w, n_leaves, (p+1)^2) array with dense rows")
+        check(lib().q2x_leaf_reduce_weighted(self._h, n_elem, int(p), _ptr(elem), n_w, _ptr(weights),
+                                             weights.stride(0), n_leaves, _ptr(leaf_off), _ptr(coef),
+                                             coef.stride(0), int(bool(accumulate))), self._h)
+        return coef
+
+    def segments_vector(self, vxyz, idx, current, leaf_off, leaf_c, leaf_rho=None, leaf_p=None, coef3=None,
+                        accumulate=False):
         """Coefficients of the three components of a vector line density
         (current (3, n_elem), constant per segment), as (3, n_leaves,
-        (p+1)^2): one segment pass per component (Eq. (st3): the moments are
-        geometric and multiply each component)."""
-        _need(current, torch.float64, "current", (3, idx.shape[1]))
-        n_leaves = leaf_c.shape[1]
-        out = torch.empty((3, n_leaves, n_coef(self.p_max)), dtype=torch.float64, device=vxyz.device)
-        for k in range(3):
-            self.segments(vxyz, idx, current[k].contiguous(), leaf_off, leaf_c, leaf_rho, leaf_p, coef=out[k])
-        return out
+        (p+1)^2) (q2x_segments_vector: one recursion pass for all three
+        components, Eq. (st3))."""
+        n_vert, n_elem = self._geom(vxyz, idx, 2)
+        _need(current, torch.float64, "current", (3, n_elem))
+        if leaf_off is None:
+            raise ValueError("segments_vector needs leaf_off")
+        n_leaves = self._leaf_args(n_elem, leaf_off, leaf_c, leaf_rho, leaf_p)
+        nc = n_coef(self.p_max)
+        if coef3 is None:
+            if accumulate:
+                raise ValueError("accumulate=True needs an output tensor")
+            coef3 = torch.empty((3, n_leaves, nc), dtype=torch.float64, device=vxyz.device)
+        _need(coef3, torch.float64, "coef3", (3, n_leaves, nc))
+        check(lib().q2x_segments_vector(self._h, n_elem, n_vert, _ptr(vxyz), _ptr(idx), _ptr(current), n_leaves,
+                                        _ptr(leaf_off), _ptr(leaf_c), _ptr(leaf_rho), _ptr(leaf_p), _ptr(coef3),
+                                        int(bool(accumulate))), self._h)
+        return coef3
 
     def evaluate_curl(self, coef3, exp_c, tgt, tgt_off=None, exp_idx=None, out=None, accumulate=False, p=None):
         """curl of the far field of vector expansions coef3 (3, n_exp,

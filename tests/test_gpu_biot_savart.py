@@ -78,3 +78,57 @@ def test_curl_needs_coeff_norm(q2x):
         plan.evaluate_curl(c3, torch.zeros((3, 1), dtype=torch.float64, device="cuda"),
                            torch.ones((3, 2), dtype=torch.float64, device="cuda"))
     assert ei.value.status == 7
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_vector_chunked_and_per_component_agree(q2x, prec):
+    """The fused pass (one recursion, weighted reduce) against one scalar
+    segment pass per component; leaf degrees, an empty leaf, no leaf scales
+    and accumulation included."""
+    p = 10
+    prob = random_problem("segment", [23, 0, 9, 40, 1], seed=15, p=p, size=0.05, spread=0.3,
+                          leaf_p=[10, 4, 7, 10, 0])
+    rng = np.random.default_rng(16)
+    cur = rng.uniform(-1, 1, (3, prob["idx"].shape[1]))
+    d = {k: T(v) for k, v in prob.items() if hasattr(v, "shape")}
+    plan = q2x.Plan(p, precision=prec)
+    one = plan.segments_vector(d["vxyz"], d["idx"], T(cur), d["leaf_off"], d["leaf_c"], d["leaf_rho"], d["leaf_p"])
+    # without leaf scales (computed internally for FP32, unit scale for FP64) and accumulating
+    acc = plan.segments_vector(d["vxyz"], d["idx"], T(cur), d["leaf_off"], d["leaf_c"], None, d["leaf_p"],
+                               coef3=one.clone(), accumulate=True)
+    ref = torch.stack([plan.segments(d["vxyz"], d["idx"], T(cur[k]), d["leaf_off"], d["leaf_c"], d["leaf_rho"],
+                                     d["leaf_p"]) for k in range(3)])
+    plan.sync()
+    scale = ref.abs().max().item()
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    assert (one - ref).abs().max().item() <= tol * scale
+    assert (acc - 2 * ref).abs().max().item() <= 2 * tol * scale
+    assert torch.all(one[:, 1] == 0)  # the empty leaf
+    for L, pl in enumerate([10, 4, 7, 10, 0]):  # moments above each leaf's degree are zero
+        assert torch.all(one[:, L, (pl + 1) ** 2:] == 0)
+
+
+def test_leaf_reduce_weighted(q2x):
+    rng = np.random.default_rng(17)
+    p = 5
+    sizes = [0, 5, 1, 300, 0, 17]
+    import workloads as W
+    off = W.csr_from_leaf_of(np.repeat(np.arange(len(sizes)), sizes), len(sizes))
+    n = int(off[-1])
+    elem = rng.standard_normal((n, 36))
+    w = rng.standard_normal((4, n))
+    plan = q2x.Plan(p)
+    for nw in (1, 2, 3, 4):
+        got = plan.leaf_reduce_weighted(T(elem), p, T(off), T(w[:nw])).cpu().numpy()
+        acc0 = torch.full((nw, len(sizes), 36), 2.0, dtype=torch.float64, device="cuda")
+        acc = plan.leaf_reduce_weighted(T(elem), p, T(off), T(w[:nw]), coef=acc0, accumulate=True).cpu().numpy()
+        plan.sync()
+        for j in range(nw):
+            for L in range(len(sizes)):
+                ref = np.zeros(36)
+                for e in range(off[L], off[L + 1]):
+                    ref = ref + w[j, e] * elem[e]
+                assert np.max(np.abs(got[j, L] - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+        assert np.array_equal(acc, got + 2.0)
+    with pytest.raises(ValueError):  # at most four weight rows
+        plan.leaf_reduce_weighted(T(elem), p, T(off), T(np.zeros((5, n))))
