@@ -568,17 +568,25 @@ __device__ __forceinline__ void reduce_chunk(const ElemArgs& a, const RangeCtx& 
     const int nlay = (want0 ? 1 : 0) + (want1 ? 1 : 0);
     const int total = nlay * ncols;
     if (per_elem) {
-        // rows unrolled so that several rows' stores are in flight
+        // the (row, column) items of the chunk in row-major order, 32 at a
+        // time, unrolled so that several stores are in flight (a row is one
+        // element's complete expansion)
+        const int n_items = nrows * total;
+        int r = 0, tc = lane;
+        while (tc >= total && r < nrows) {
+            tc -= total;
+            ++r;
+        }
 #pragma unroll 4
-        for (int r = 0; r < nrows; ++r) {
-            const long long L = rowleaf[r];
-            const int info = rowinfo[r];
-#pragma unroll 1
-            for (int tc = lane; tc < total; tc += 32) {
-                const int second = (tc >= ncols) ? 1 : 0;
-                const int ly = want0 ? second : 1;
-                const int j = tc - second * ncols;
-                flush_value<T>(a, rc, ly, c0 + j, tile[(ly * CH + j) * LD + r], L, info);
+        for (int i = lane; i < n_items; i += 32) {
+            const int second = (tc >= ncols) ? 1 : 0;
+            const int ly = want0 ? second : 1;
+            const int j = tc - second * ncols;
+            flush_value<T>(a, rc, ly, c0 + j, tile[(ly * CH + j) * LD + r], rowleaf[r], rowinfo[r]);
+            tc += 32;
+            while (tc >= total) {
+                tc -= total;
+                ++r;
             }
         }
         return;
