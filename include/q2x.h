@@ -403,7 +403,7 @@ q2x_status q2x_leaf_reduce(q2x_plan_t plan, int64_t n_elem, int p, const double*
  * arguments of q2x_segments (leaf_off required).  The moments are geometric
  * and each component multiplies them, so the recursion runs once per
  * element: a per-element pass stores each element's unfinished moments about
- * its leaf's centre (chunks of at most 1 GiB of rows, stream-ordered
+ * its leaf's centre (chunks of at most 4 GiB of rows, stream-ordered
  * allocation on the plan's stream), then one weighted segmented sum per
  * (leaf, column) forms the three components and finishes them.  Same
  * results as three q2x_segments calls with the components as densities, up

@@ -732,8 +732,9 @@ q2x_status q2x_segments_vector(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, 
     check_leaf_off_kernel<<<(unsigned)((n_leaves + 1 + 255) / 256), 256, 0, plan->stream>>>(leaf_off, n_leaves, n_elem,
                                                                                            plan->d_err);
     plan->launches += 1;
-    // elements in chunks whose unfinished rows take at most 1 GiB
-    const int64_t m_max = std::min<int64_t>(n_elem, std::max<int64_t>(1024, ((int64_t)1 << 30) / (8 * np)));
+    // elements in chunks whose unfinished rows take at most 4 GiB (one chunk
+    // for a few million elements: every chunk pays a kernel tail)
+    const int64_t m_max = std::min<int64_t>(n_elem, std::max<int64_t>(1024, ((int64_t)1 << 32) / (8 * np)));
     const bool need_rho = plan->prec == 1 && leaf_rho == nullptr;  // FP32 needs the leaf scale
     const size_t b_rows = align_up(sizeof(double) * (size_t)m_max * np, 256);
     const size_t b_ec = align_up(sizeof(double) * 3 * (size_t)m_max, 256);
