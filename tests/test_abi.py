@@ -52,3 +52,27 @@ def test_null_plan_is_an_argument_error(so):
     so.q2x_last_error.restype = ctypes.c_char_p
     so.q2x_last_error.argtypes = [ctypes.c_void_p]
     assert so.q2x_last_error(None)  # a message is recorded
+
+
+def test_null_plan_rejected_by_every_compute_entry(so):
+    """Each compute entry point checks its plan before touching the device:
+    called through the same ctypes signatures the binding uses, with a NULL
+    plan and zero sizes, every one returns Q2X_ERR_ARG (1)."""
+    from paper_2107_10942_gb300._lib import _SIGNATURES
+    skip = {"q2x_plan", "q2x_last_error", "q2x_launch_count", "q2x_workspace_bytes", "q2x_plan_destroy",
+            "q2x_batch_destroy", "q2x_batch_info", "q2x_device_errors", "q2x_plan_kernel_timing"}
+    checked = []
+    for name, argtypes in _SIGNATURES.items():
+        if name in skip or not hasattr(so, name):
+            continue
+        f = getattr(so, name)
+        f.restype = ctypes.c_int
+        f.argtypes = argtypes
+        args = [None if t is ctypes.c_void_p else t(0) if t in (ctypes.c_int, ctypes.c_int64) else None
+                for t in argtypes]
+        st = f(*args)
+        assert st == 1, (name, st)
+        checked.append(name)
+    for required in ("q2x_nearfield", "q2x_segments_vector", "q2x_leaf_reduce_weighted", "q2x_translate",
+                     "q2x_evaluate", "q2x_evaluate_curl", "q2x_galerkin_triangles"):
+        assert required in checked
