@@ -388,6 +388,15 @@ def main():
         cpu = {"value": 2 * ne * nc / dt, "unit": UNIT, "cores": orc.max_threads(), "kind": "oracle",
                "sample": "%d of %d triangles (%d whole leaves), single+double layer, FP64 Gauss quadrature "
                          "(%d nodes/direction), OpenMP; %.1f s" % (ne, n_elem, len(leaves), (P + 5) // 2, dt)}
+        # the same oracle on one core, on a sample sized for about a quarter of that time
+        leaves1 = sample_leaves(prob, max(200, int(ne * min(1.0, 0.25 / max(orc.max_threads(), 1)))))
+        sub1 = sub_problem(prob, leaves1)
+        t0 = time.perf_counter()
+        oracle_run(orc, sub1, nthreads=1)
+        dt1 = time.perf_counter() - t0
+        ne1 = sub1["idx"].shape[1]
+        cpu["single_core"] = {"value": 2 * ne1 * nc / dt1, "unit": UNIT, "cores": 1,
+                              "sample": "%d triangles (%d whole leaves), %.1f s" % (ne1, len(leaves1), dt1)}
         for prec in ("fp64", "fp32"):
             cs, cd = outs[prec]
             errs[prec] = {"single": norm_err(cs[leaves], ref_s, prob["leaf_rho"][leaves], 0),
