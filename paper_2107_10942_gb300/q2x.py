@@ -42,6 +42,17 @@ def _need(t, dtype, name, shape=None):
     return t
 
 
+class PlanGraph:
+    """A captured sequence of q2x calls (Plan.capture)."""
+
+    def __init__(self, graph, kernels):
+        self.graph = graph
+        self.kernels = kernels  # kernels launched per replay
+
+    def replay(self):
+        self.graph.replay()
+
+
 class Plan:
     """A q2x_plan: degree bound, normalisation, precision, stream and the
     library-owned workspace.  Calls are asynchronous on the plan's stream;
@@ -78,6 +89,26 @@ class Plan:
     def set_stream(self, stream):
         self._stream = stream
         check(lib().q2x_plan_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)), self._h)
+
+    def capture(self, fn):
+        """Record the q2x calls that fn() makes on this plan as one CUDA graph
+        and return a PlanGraph whose replay() re-runs them on the current
+        stream with one host launch (same buffers; their contents may
+        change between replays).  fn runs once eagerly first, so that the
+        plan's workspace and kernel attributes are set before the capture."""
+        fn()
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        old = self._stream
+        n0 = self.launch_count()
+        self.set_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        try:
+            with torch.cuda.graph(graph, stream=side):
+                fn()
+        finally:
+            self.set_stream(old)
+        return PlanGraph(graph, self.launch_count() - n0)
 
     def sync(self):
         check(lib().q2x_sync(self._h), self._h)
