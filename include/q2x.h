@@ -301,6 +301,26 @@ q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const double* sr
                          const double* src_c, int64_t n_dst, const int64_t* dst_off,
                          const double* dst_c, double* dst_coef, int accumulate);
 
+/* The solid harmonics R_n^m(t), n <= p, of n_t translation vectors t
+ * (double[3 * n_t] SoA, device) into rt (double[n_t * (p+1)^2], device),
+ * packed like the coefficients: Re R_n^m at n^2+n+m for m >= 0 and
+ * Im R_n^|m| at n^2+n-|m| (R_n^{-m} = (-1)^m conj R_n^m).  Built by the
+ * point recursion of Eq. (rec2), as q2x_translate does per source; a tree
+ * whose shifts are fixed computes them once (an octree level has eight).
+ * FP64; p <= the plan's p_max. */
+q2x_status q2x_translation_rows(q2x_plan_t plan, int p, int64_t n_t, const double* t, double* rt);
+
+/* q2x_translate with R(t) read from precomputed rows instead of built per
+ * source: source s uses row t_idx[s] (int32, device) of rt (n_t rows from
+ * q2x_translation_rows), which must hold R(c_src - c_dst) for the source's
+ * destination; the centres are then not needed.  An index outside
+ * [0, n_t) sets bit 1 of the device error word and that source adds zero.
+ * Other arguments and the results as q2x_translate (up to the rounding of
+ * R_n^{-m} taken from R_n^m). */
+q2x_status q2x_translate_rt(q2x_plan_t plan, int p, int64_t n_src, const double* src_coef, int64_t n_t,
+                            const double* rt, const int32_t* t_idx, int64_t n_dst, const int64_t* dst_off,
+                            double* dst_coef, int accumulate);
+
 /* Far-field evaluation (the M2P step fed by the leaf or box coefficients):
  * out[t] (+)= sum over the expansions e listed for target t of
  *   phi_e(x_t) = sum_{n<=p} sum_{|m|<=n} F_n^m S_n^m(x_t - c_e)      (Eq. (bas3))

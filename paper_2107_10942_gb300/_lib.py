@@ -35,6 +35,8 @@ _SIGNATURES = {
     "q2x_triangles_double": [_p, _i64, _i64, _p, _p, _i, _p, _i64, _p, _p, _p, _p, _p, _i],
     "q2x_leaf_reduce": [_p, _i64, _i, _p, _i64, _p, _p, _i],
     "q2x_translate": [_p, _i, _i64, _p, _p, _i64, _p, _p, _p, _i],
+    "q2x_translation_rows": [_p, _i, _i64, _p, _p],
+    "q2x_translate_rt": [_p, _i, _i64, _p, _i64, _p, _p, _i64, _p, _p, _i],
     "q2x_evaluate": [_p, _i, _i64, _p, _p, _i64, _p, _p, _p, _p, _i],
     "q2x_evaluate_curl": [_p, _i, _i64, _p, _p, _i64, _p, _p, _p, _p, _i],
     "q2x_segments_vector": [_p, _i64, _i64, _p, _p, _p, _i64, _p, _p, _p, _p, _p, _i],

@@ -40,7 +40,18 @@ struct TransArgs {
     double* dst_coef;
     double2* rows;  // [n_src][n_out] translated rows, complex (n, m >= 0)
     unsigned* err;
+    const double* rt = nullptr;     // precomputed packed R(t) rows (NULL: built per source)
+    const int32_t* t_idx = nullptr;  // row of rt for each source
+    int64_t n_t = 0;
 };
+
+// R_k^l(t) for |l| <= k <= p into Rc (complex, index k^2 + k + l) and -R
+// into Rc + TR_NP_MAX, by the point recursion of Eq. (rec2); one warp.
+__device__ void build_r(double2* Rc, int p, double tx, double ty, double tz, int lane);
+
+// Packed real row of R(t) (Re at n^2+n+m, Im at n^2+n-m, m > 0) unpacked
+// into Rc and -Rc (R_n^{-m} = (-1)^m conj R_n^m); one warp.
+__device__ void unpack_r(double2* Rc, const double* __restrict__ row, int np, int lane);
 
 // degree and order of output o = n(n+1)/2 + m, 0 <= m <= n
 __device__ __forceinline__ void out_nm(int o, int& n, int& m)
@@ -118,57 +129,8 @@ constexpr TermTab make_terms()
 }
 static __device__ const TermTab g_terms = make_terms();
 
-// One warp per source (or, for the few sources at the top of a tree, one
-// CTA of four warps per source): the source's complex row and R(t) (and
-// -R(t)) in each warp's shared memory, then the contraction over the
-// flattened term list, each lane a contiguous run of terms (equal work per
-// lane).  Outputs wholly inside a lane's run are written by that lane; the
-// partial sums of an output split across runs are added in run order by the
-// lane whose run holds its first part.
-__global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransArgs a)
+__device__ void build_r(double2* Rc, int p, double tx, double ty, double tz, int lane)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int64_t s = a.cta_per_source ? (int64_t)blockIdx.x : (int64_t)blockIdx.x * TR_WARPS + wib;
-    const int nsub = a.cta_per_source ? TR_WARPS : 1;  // runs of 32 lanes sharing the source
-    const int sub = a.cta_per_source ? wib : 0;
-    if (s >= a.n_src) return;
-    const int p = a.p, np = a.np;
-    double2* Fc = reinterpret_cast<double2*>(smem_raw) + (size_t)wib * 3 * TR_NP_MAX;
-    double2* Rc = Fc + TR_NP_MAX;  // R at [0, TR_NP_MAX), -R at [TR_NP_MAX, 2 TR_NP_MAX)
-    __shared__ int s_head_o[TR_WARPS][32], s_tail_o[TR_WARPS][32];
-    __shared__ double2 s_head_v[TR_WARPS][32], s_tail_v[TR_WARPS][32];
-    // destination of s: the range of dst_off holding it (clamped; ranges are
-    // validated by the combine kernel)
-    int64_t lo = 0, hi = a.n_dst - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (__ldg(a.dst_off + mid) <= s)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const int64_t d = lo;
-
-    // ---- complex source row F[n][m], m = -n..n (Eq. (bas2.1) for m < 0)
-    const double* src = a.src_coef + s * (int64_t)np;
-    for (int k = lane; k < np; k += 32) {
-        int n, m;
-        col_nm(k, n, m);
-        const int am = m < 0 ? -m : m;
-        const int k0 = n * n + n;
-        const double re = __ldg(src + k0 + am);
-        const double im = am ? __ldg(src + k0 - am) : 0.0;
-        if (m >= 0)
-            Fc[k] = make_double2(re, im);
-        else
-            Fc[k] = (am & 1) ? make_double2(-re, im) : make_double2(re, -im);
-    }
-    // ---- R_k^l(t), t = c_src - c_dst, row by row
-    const double tx = __ldg(a.src_c + s) - __ldg(a.dst_c + d);
-    const double ty = __ldg(a.src_c + a.n_src + s) - __ldg(a.dst_c + a.n_dst + d);
-    const double tz = __ldg(a.src_c + 2 * a.n_src + s) - __ldg(a.dst_c + 2 * a.n_dst + d);
     if (lane == 0) {
         Rc[0] = make_double2(1.0, 0.0);
         Rc[TR_NP_MAX] = make_double2(-1.0, 0.0);
@@ -204,6 +166,119 @@ __global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransA
         }
         __syncwarp();
     }
+}
+
+__device__ void unpack_r(double2* Rc, const double* __restrict__ row, int np, int lane)
+{
+    for (int k = lane; k < np; k += 32) {
+        int n, m;
+        col_nm(k, n, m);
+        const int am = m < 0 ? -m : m;
+        const int k0 = n * n + n;
+        const double re = __ldg(row + k0 + am);
+        const double im = am ? __ldg(row + k0 - am) : 0.0;
+        const double2 v = (m >= 0) ? make_double2(re, im)
+                                   : ((am & 1) ? make_double2(-re, im) : make_double2(re, -im));
+        Rc[k] = v;
+        Rc[TR_NP_MAX + k] = make_double2(-v.x, -v.y);
+    }
+}
+
+// One warp per translation vector: R(t) built in shared memory, then packed.
+__global__ void __launch_bounds__(TR_WARPS * 32) q2x_translation_rows_kernel(int p, int64_t n_t,
+                                                                            const double* __restrict__ t,
+                                                                            double* rt)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * TR_WARPS + wib;
+    if (i >= n_t) return;
+    double2* Rc = reinterpret_cast<double2*>(smem_raw) + (size_t)wib * 2 * TR_NP_MAX;
+    build_r(Rc, p, __ldg(t + i), __ldg(t + n_t + i), __ldg(t + 2 * n_t + i), lane);
+    const int np = (p + 1) * (p + 1);
+    double* out = rt + i * (int64_t)np;
+    for (int k = lane; k < np; k += 32) {
+        int n, m;
+        col_nm(k, n, m);
+        const double2 v = Rc[n * n + n + (m < 0 ? -m : m)];
+        out[k] = (m >= 0) ? v.x : v.y;
+    }
+}
+
+// One warp per source (or, for the few sources at the top of a tree, one
+// CTA of four warps per source): the source's complex row and R(t) (and
+// -R(t)) in shared memory -- the warp's own copy, or one copy per CTA built
+// by its first warp -- then the contraction over the
+// flattened term list, each lane a contiguous run of terms (equal work per
+// lane).  Outputs wholly inside a lane's run are written by that lane; the
+// partial sums of an output split across runs are added in run order by the
+// lane whose run holds its first part.
+__global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t s = a.cta_per_source ? (int64_t)blockIdx.x : (int64_t)blockIdx.x * TR_WARPS + wib;
+    const int nsub = a.cta_per_source ? TR_WARPS : 1;  // runs of 32 lanes sharing the source
+    const int sub = a.cta_per_source ? wib : 0;
+    if (s >= a.n_src) return;
+    const int p = a.p, np = a.np;
+    // one copy of the source row and R(t) per source: per warp, or shared by
+    // the CTA's warps (built by its first warp)
+    const bool cta = a.cta_per_source != 0;
+    double2* Fc = reinterpret_cast<double2*>(smem_raw) + (size_t)(cta ? 0 : wib) * 3 * TR_NP_MAX;
+    double2* Rc = Fc + TR_NP_MAX;  // R at [0, TR_NP_MAX), -R at [TR_NP_MAX, 2 TR_NP_MAX)
+    __shared__ int s_head_o[TR_WARPS][32], s_tail_o[TR_WARPS][32];
+    __shared__ double2 s_head_v[TR_WARPS][32], s_tail_v[TR_WARPS][32];
+    // destination of s: the range of dst_off holding it (clamped; ranges are
+    // validated by the combine kernel)
+    int64_t lo = 0, hi = a.n_dst - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(a.dst_off + mid) <= s)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int64_t d = lo;
+
+    if (!cta || wib == 0) {
+        // ---- complex source row F[n][m], m = -n..n (Eq. (bas2.1) for m < 0)
+        const double* src = a.src_coef + s * (int64_t)np;
+        for (int k = lane; k < np; k += 32) {
+            int n, m;
+            col_nm(k, n, m);
+            const int am = m < 0 ? -m : m;
+            const int k0 = n * n + n;
+            const double re = __ldg(src + k0 + am);
+            const double im = am ? __ldg(src + k0 - am) : 0.0;
+            if (m >= 0)
+                Fc[k] = make_double2(re, im);
+            else
+                Fc[k] = (am & 1) ? make_double2(-re, im) : make_double2(re, -im);
+        }
+        // ---- R_k^l(t), t = c_src - c_dst: a precomputed row, or the recursion
+        if (a.rt) {
+            int ti = __ldg(a.t_idx + s);
+            if (ti < 0 || ti >= a.n_t) {
+                if (lane == 0) atomicOr(a.err, 1u);
+                ti = -1;
+            }
+            if (ti >= 0) {
+                unpack_r(Rc, a.rt + (int64_t)ti * np, np, lane);
+            } else {
+                for (int k = lane; k < np; k += 32) Rc[k] = Rc[TR_NP_MAX + k] = make_double2(0.0, 0.0);
+            }
+            __syncwarp();
+        } else {
+            const double tx = __ldg(a.src_c + s) - __ldg(a.dst_c + d);
+            const double ty = __ldg(a.src_c + a.n_src + s) - __ldg(a.dst_c + a.n_dst + d);
+            const double tz = __ldg(a.src_c + 2 * a.n_src + s) - __ldg(a.dst_c + 2 * a.n_dst + d);
+            build_r(Rc, p, tx, ty, tz, lane);
+        }
+    }
+    if (cta) __syncthreads();  // the shared row and R(t) are complete
     // ---- contraction over this lane's run of terms
     double2* row = a.rows + s * (int64_t)a.n_out;
     const uint32_t* code = g_terms.code[a.norm ? 1 : 0];
@@ -323,9 +398,10 @@ __global__ void q2x_translate_combine(const TransArgs a)
 
 }  // namespace q2x
 
-extern "C" q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const double* src_coef,
-                                    const double* src_c, int64_t n_dst, const int64_t* dst_off,
-                                    const double* dst_c, double* dst_coef, int accumulate)
+static q2x_status translate_impl(q2x_plan_t plan, int p, int64_t n_src, const double* src_coef,
+                                 const double* src_c, int64_t n_dst, const int64_t* dst_off, const double* dst_c,
+                                 double* dst_coef, int accumulate, const double* rt, const int32_t* t_idx,
+                                 int64_t n_t)
 {
     if (!plan) return q2x_fail(nullptr, Q2X_ERR_ARG, "plan is NULL");
     if (p < 0 || p > plan->p_max) return q2x_fail(plan, Q2X_ERR_RANGE, "p = %d outside 0..%d", p, plan->p_max);
@@ -333,8 +409,9 @@ extern "C" q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const
     if (accumulate != 0 && accumulate != 1) return q2x_fail(plan, Q2X_ERR_ARG, "accumulate must be 0 or 1");
     if (n_dst == 0) return Q2X_OK;
     if (n_dst > 0x7fffffffLL || n_src > ((int64_t)1 << 36)) return q2x_fail(plan, Q2X_ERR_ARG, "size too large");
-    if (!dst_off || !dst_c || !dst_coef) return q2x_fail(plan, Q2X_ERR_ARG, "NULL destination array");
-    if (n_src > 0 && (!src_coef || !src_c)) return q2x_fail(plan, Q2X_ERR_ARG, "NULL source array");
+    if (!dst_off || !dst_coef || (!rt && !dst_c)) return q2x_fail(plan, Q2X_ERR_ARG, "NULL destination array");
+    if (n_src > 0 && (!src_coef || (!rt && !src_c) || (rt && (!t_idx || n_t <= 0))))
+        return q2x_fail(plan, Q2X_ERR_ARG, "NULL source array or translation rows");
     cudaError_t e = cudaSetDevice(plan->device);
     if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "cudaSetDevice");
     q2x::TransArgs a;
@@ -352,6 +429,9 @@ extern "C" q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const
     a.dst_c = dst_c;
     a.dst_coef = dst_coef;
     a.err = plan->d_err;
+    a.rt = rt;
+    a.t_idx = t_idx;
+    a.n_t = n_t;
     q2x_status st = q2x_plan_workspace(plan, sizeof(double2) * (size_t)(n_src > 0 ? n_src : 1) * a.n_out);
     if (st != Q2X_OK) return st;
     a.rows = static_cast<double2*>(plan->ws);
@@ -363,7 +443,8 @@ extern "C" q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const
         // not the latency of one warp's FP64 stream
         a.cta_per_source = (n_src * 4 <= (int64_t)plan->num_sms * 8) ? 1 : 0;
         const int64_t grid = a.cta_per_source ? n_src : (n_src + q2x::TR_WARPS - 1) / q2x::TR_WARPS;
-        q2x::q2x_translate_rows<<<(unsigned)grid, q2x::TR_WARPS * 32, smem, plan->stream>>>(a);
+        const size_t smem_launch = a.cta_per_source ? smem / q2x::TR_WARPS : smem;  // one shared copy
+        q2x::q2x_translate_rows<<<(unsigned)grid, q2x::TR_WARPS * 32, smem_launch, plan->stream>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "q2x_translate_rows launch");
         plan->launches += 1;
@@ -371,6 +452,46 @@ extern "C" q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const
     q2x::q2x_translate_combine<<<(unsigned)((n_dst + 3) / 4), 128, 0, plan->stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "q2x_translate_combine launch");
+    plan->launches += 1;
+    return Q2X_OK;
+}
+
+extern "C" q2x_status q2x_translate(q2x_plan_t plan, int p, int64_t n_src, const double* src_coef,
+                                    const double* src_c, int64_t n_dst, const int64_t* dst_off,
+                                    const double* dst_c, double* dst_coef, int accumulate)
+{
+    return translate_impl(plan, p, n_src, src_coef, src_c, n_dst, dst_off, dst_c, dst_coef, accumulate, nullptr,
+                          nullptr, 0);
+}
+
+extern "C" q2x_status q2x_translate_rt(q2x_plan_t plan, int p, int64_t n_src, const double* src_coef, int64_t n_t,
+                                       const double* rt, const int32_t* t_idx, int64_t n_dst,
+                                       const int64_t* dst_off, double* dst_coef, int accumulate)
+{
+    if (!plan) return q2x_fail(nullptr, Q2X_ERR_ARG, "plan is NULL");
+    if (n_src > 0 && (!rt || !t_idx)) return q2x_fail(plan, Q2X_ERR_ARG, "NULL translation rows");
+    return translate_impl(plan, p, n_src, src_coef, nullptr, n_dst, dst_off, nullptr, dst_coef, accumulate,
+                          n_src > 0 ? rt : nullptr, t_idx, n_t);
+}
+
+extern "C" q2x_status q2x_translation_rows(q2x_plan_t plan, int p, int64_t n_t, const double* t, double* rt)
+{
+    if (!plan) return q2x_fail(nullptr, Q2X_ERR_ARG, "plan is NULL");
+    if (p < 0 || p > plan->p_max) return q2x_fail(plan, Q2X_ERR_RANGE, "p = %d outside 0..%d", p, plan->p_max);
+    if (n_t < 0) return q2x_fail(plan, Q2X_ERR_ARG, "negative size");
+    if (n_t == 0) return Q2X_OK;
+    if (!t || !rt) return q2x_fail(plan, Q2X_ERR_ARG, "NULL array");
+    if (n_t > ((int64_t)1 << 36)) return q2x_fail(plan, Q2X_ERR_ARG, "size too large");
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "cudaSetDevice");
+    const size_t smem = (size_t)q2x::TR_WARPS * 2 * q2x::TR_NP_MAX * sizeof(double2);
+    e = cudaFuncSetAttribute(q2x::q2x_translation_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "cudaFuncSetAttribute");
+    q2x::q2x_translation_rows_kernel<<<(unsigned)((n_t + q2x::TR_WARPS - 1) / q2x::TR_WARPS), q2x::TR_WARPS * 32,
+                                       smem, plan->stream>>>(p, n_t, t, rt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "q2x_translation_rows launch");
     plan->launches += 1;
     return Q2X_OK;
 }

@@ -266,6 +266,44 @@ class Plan:
                                   _ptr(dst_c), _ptr(dst_coef), int(bool(accumulate))), self._h)
         return dst_coef
 
+    def translation_rows(self, t, p=None, out=None):
+        """R_n^m(t) for the translation vectors t (3, n_t), packed like the
+        coefficients, as (n_t, (p+1)^2) (q2x_translation_rows)."""
+        p = self.p_max if p is None else int(p)
+        _need(t, torch.float64, "t")
+        if t.dim() != 2 or t.shape[0] != 3:
+            raise ValueError("t must be (3, n_t)")
+        n_t = t.shape[1]
+        if out is None:
+            out = torch.empty((n_t, n_coef(p)), dtype=torch.float64, device=t.device)
+        _need(out, torch.float64, "out", (n_t, n_coef(p)))
+        check(lib().q2x_translation_rows(self._h, p, n_t, _ptr(t), _ptr(out)), self._h)
+        return out
+
+    def translate_rt(self, src_coef, rt, t_idx, dst_off, dst_coef=None, accumulate=False, p=None):
+        """translate() with R(t) from precomputed rows: source s uses row
+        t_idx[s] of rt (q2x_translate_rt)."""
+        p = self.p_max if p is None else int(p)
+        nc = n_coef(p)
+        _need(src_coef, torch.float64, "src_coef")
+        if src_coef.dim() != 2 or src_coef.shape[1] != nc:
+            raise ValueError("src_coef must be (n_src, (p+1)^2)")
+        n_src = src_coef.shape[0]
+        _need(rt, torch.float64, "rt")
+        if rt.dim() != 2 or rt.shape[1] != nc:
+            raise ValueError("rt must be (n_t, (p+1)^2)")
+        _need(t_idx, torch.int32, "t_idx", (n_src,))
+        _need(dst_off, torch.int64, "dst_off")
+        n_dst = dst_off.shape[0] - 1
+        if dst_coef is None:
+            if accumulate:
+                raise ValueError("accumulate=True needs an output tensor")
+            dst_coef = torch.empty((n_dst, nc), dtype=torch.float64, device=src_coef.device)
+        _need(dst_coef, torch.float64, "dst_coef", (n_dst, nc))
+        check(lib().q2x_translate_rt(self._h, p, n_src, _ptr(src_coef), rt.shape[0], _ptr(rt), _ptr(t_idx), n_dst,
+                                     _ptr(dst_off), _ptr(dst_coef), int(bool(accumulate))), self._h)
+        return dst_coef
+
 
     def evaluate(self, coef, exp_c, tgt, tgt_off=None, exp_idx=None, out=None, accumulate=False, p=None):
         """Far-field potential at the targets tgt (3, n_tgt) of the expansions

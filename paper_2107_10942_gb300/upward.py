@@ -106,20 +106,33 @@ class Upward:
         self.identity = len(deep) == nl and bool(np.array_equal(deep, np.arange(nl)))
         self.deep_idx = torch.from_numpy(deep).to(device)
         self.dev = []
+        # per level: the distinct shifts t = c_src - c_dst of its translations
+        # (eight on an octree level) and each source's shift, so that R(t) is
+        # computed once for the tree (q2x_translation_rows) instead of once
+        # per translation and pass
+        self.rt = []
+        src_c_h = lc[:, deep]
         for lv in self.levels:
             off = torch.from_numpy(lv["dst_off"]).to(device)
             c = torch.from_numpy(np.ascontiguousarray(lv["c"])).to(device)
             out = torch.empty((c.shape[1], nc), dtype=torch.float64, device=device)
+            dest = np.repeat(np.arange(lv["c"].shape[1]), np.diff(lv["dst_off"]))
+            t = src_c_h - lv["c"][:, dest]
+            t_tab, t_idx = np.unique(t.T, axis=0, return_inverse=True)
+            rt = plan.translation_rows(torch.from_numpy(np.ascontiguousarray(t_tab.T)).to(device), self.p)
+            self.rt.append((rt, torch.from_numpy(t_idx.reshape(-1).astype(np.int32)).to(device)))
             # the boxes of this depth as the next level's sources, gathered
             # from [internal rows of this level; leaf rows]
             n_int = c.shape[1]
             gidx = np.array([k if kind == 0 else n_int + k for kind, k in lv["nodes"]], dtype=np.int64)
             if len(gidx) == n_int and np.array_equal(gidx, np.arange(n_int)):
                 self.dev.append((off, c, out, None, None))
+                src_c_h = lv["c"]
             else:
                 allc = np.concatenate([lv["c"], lc], axis=1)
                 nodes_c = torch.from_numpy(np.ascontiguousarray(allc[:, gidx])).to(device)
                 self.dev.append((off, c, out, torch.from_numpy(gidx).to(device), nodes_c))
+                src_c_h = allc[:, gidx]
 
     @staticmethod
     def _deepest_rows(lc, lo, size, depth):
@@ -156,12 +169,19 @@ class Upward:
         self._graph.replay()
         return self._graph_outs
 
-    def run(self, leaf_coef):
+    def run(self, leaf_coef, precomputed_shifts=True):
+        """The pass over the leaf rows leaf_coef (one row per leaf, in the
+        order of leaf_c); returns one tensor per depth, root last.  With
+        precomputed_shifts=False each translation builds its own R(t)
+        (q2x_translate) instead of reading the tree's shift rows."""
         src = leaf_coef if self.identity else leaf_coef.index_select(0, self.deep_idx)
         src_c = self.leaf_c if self.identity else self.leaf_c.index_select(1, self.deep_idx)
         outs = []
-        for off, c, out, gidx, nodes_c in self.dev:
-            self.plan.translate(src, src_c, off, c, dst_coef=out, p=self.p)
+        for (off, c, out, gidx, nodes_c), (rt, t_idx) in zip(self.dev, self.rt):
+            if precomputed_shifts:
+                self.plan.translate_rt(src, rt, t_idx, off, dst_coef=out, p=self.p)
+            else:
+                self.plan.translate(src, src_c, off, c, dst_coef=out, p=self.p)
             outs.append(out)
             if gidx is None:
                 src, src_c = out, c

@@ -208,3 +208,58 @@ def test_upward_graph_replay_bitwise(q2x, adaptive):
     plan.sync()
     assert all(torch.equal(a, b) for a, b in zip(eager2, got2))
     assert not torch.equal(eager[-1], eager2[-1])
+
+
+def test_translation_rows_match_oracle_harmonics(q2x, orc):
+    """q2x_translation_rows against the oracle's Cartesian R_n^m (Eq. bas1),
+    in the coefficients' real packing."""
+    p = 14
+    rng = np.random.default_rng(41)
+    t = rng.normal(size=(3, 9)) * 0.3
+    t[:, 0] = 0.0  # the zero shift: R_0^0 = 1, all else 0
+    plan = q2x.Plan(p, precision="fp64")
+    rows = plan.translation_rows(torch.from_numpy(t).cuda()).cpu().numpy()
+    plan.sync()
+    for i in range(t.shape[1]):
+        R = orc.rnm(t[:, i], p)
+        ref = np.zeros((p + 1) ** 2)
+        for n in range(p + 1):
+            for m in range(n + 1):
+                ref[n * n + n + m] = R[n * n + n + m].real
+                if m:
+                    ref[n * n + n - m] = R[n * n + n + m].imag
+        assert np.max(np.abs(rows[i] - ref)) <= 1e-14 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_upward_precomputed_shifts_agree(q2x, adaptive):
+    """The pass with the tree's precomputed shift rows against the pass that
+    builds R(t) per translation, and a bad shift index flagged."""
+    from paper_2107_10942_gb300.upward import Upward
+    p = 10
+    if adaptive:
+        m = W.cfg_mixed_ball(n_fil=20, n_steps=60, tri_level=3, n_tri=800, tet_spacing=0.25, n_tet=600,
+                             max_per_leaf=120, max_depth=8, p_lo=p, p_hi=p, seed=12)
+        leaf_c, lo, size, depth = m["leaf_c"], -1.0, 2.0, m["leaf_depth"]
+    else:
+        prob = W.cfg_sphere_linear(level=4, depth=3, p=p)
+        leaf_c, lo, size, depth = prob["leaf_c"], -1.125, 2.25, 3
+    nl = leaf_c.shape[1]
+    plan = q2x.Plan(p, precision="fp64")
+    gen = torch.Generator(device="cuda").manual_seed(6)
+    leaf = torch.randn((nl, (p + 1) ** 2), dtype=torch.float64, device="cuda", generator=gen)
+    up = Upward(plan, leaf_c, lo, size, depth)
+    assert all(rt.shape[0] <= 8 for rt, _ in up.rt[:1]) or adaptive  # an octree level has eight shifts
+    fast = [x.clone() for x in up.run(leaf)]
+    slow = [x.clone() for x in up.run(leaf, precomputed_shifts=False)]
+    plan.sync()
+    for a, b in zip(fast, slow):
+        assert (a - b).abs().max().item() <= 1e-13 * b.abs().max().item()
+    rt, t_idx = up.rt[0]
+    bad = t_idx.clone()
+    bad[0] = rt.shape[0]
+    off, c, out, _, _ = up.dev[0]
+    src = leaf if up.identity else leaf.index_select(0, up.deep_idx)
+    plan.translate_rt(src, rt, bad, off, dst_coef=out.clone(), p=p)
+    with pytest.raises(q2x.Q2XError):
+        plan.sync()
