@@ -5,7 +5,6 @@ from __future__ import annotations
 
 import ctypes
 
-import numpy as np
 import torch
 
 from ._lib import check, lib
