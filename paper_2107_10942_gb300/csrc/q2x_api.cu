@@ -183,13 +183,12 @@ __global__ void leaf_reduce_kernel(const double* __restrict__ elem, int np, int6
                                    int accumulate)
 {
     constexpr int U = 8;
-    const int lane = threadIdx.x & 31;
-    const int groups = (np + 31) >> 5;
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t L = gw / groups;
+    // one thread per (leaf, column), leaves' columns back to back, so that a
+    // warp is full even where a leaf's last columns do not fill one
+    const int64_t unit = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t L = unit / np;
     if (L >= n_leaves) return;
-    const int c = (int)(gw - L * groups) * 32 + lane;
-    if (c >= np) return;
+    const int c = (int)(unit - L * np);
     // clamped: a bad leaf_off is reported by check_leaf_off_kernel, never read past
     const int64_t e0 = min(max(off[L], (int64_t)0), n_elem);
     const int64_t e1 = min(max(off[L + 1], e0), n_elem);
@@ -217,6 +216,7 @@ __global__ void leaf_reduce_weighted_kernel(const double* __restrict__ elem, int
                                             int accumulate)
 {
     constexpr int U = 8;
+    // one warp per (leaf, 32 columns): the leaf's weights are read once per warp
     const int lane = threadIdx.x & 31;
     const int groups = (np + 31) >> 5;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -286,6 +286,7 @@ __global__ void vector_reduce_kernel(const double* __restrict__ rows, int np, in
                                      double* coef, int accumulate)
 {
     constexpr int U = 8;
+    // one warp per (leaf, 32 columns): the leaf's weights are read once per warp
     const int lane = threadIdx.x & 31;
     const int groups = (np + 31) >> 5;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -697,8 +698,8 @@ q2x_status q2x_leaf_reduce(q2x_plan_t plan, int64_t n_elem, int p, const double*
     check_leaf_off_kernel<<<(unsigned)((n_leaves + 1 + 255) / 256), 256, 0, plan->stream>>>(leaf_off, n_leaves, n_elem,
                                                                                            plan->d_err);
     const int warps = 8;
-    const int64_t units = n_leaves * (int64_t)((np + 31) / 32);
-    leaf_reduce_kernel<<<(unsigned)((units + warps - 1) / warps), warps * 32, 0, plan->stream>>>(
+    const int64_t units = n_leaves * (int64_t)np;  // (leaf, column) threads
+    leaf_reduce_kernel<<<(unsigned)((units + warps * 32 - 1) / (warps * 32)), warps * 32, 0, plan->stream>>>(
         elem, np, n_elem, n_leaves, leaf_off, coef, accumulate);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(plan, e, "leaf_reduce launch");
@@ -771,7 +772,7 @@ q2x_status q2x_segments_vector(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, 
         rho = r;
     }
     using C = q2x::Chain<q2x::KIND_SEG, q2x::DENS_CONST>;
-    const int64_t units = n_leaves * (int64_t)((np + 31) / 32);
+    const int64_t units = n_leaves * (int64_t)((np + 31) / 32);  // (leaf, 32-column group) warps
     for (int64_t e0 = 0; st == Q2X_OK && e0 < n_elem; e0 += m_max) {
         const int64_t m = std::min(m_max, n_elem - e0);
         vector_gather_kernel<<<(unsigned)((m + 255) / 256), 256, 0, plan->stream>>>(
@@ -818,7 +819,7 @@ q2x_status q2x_leaf_reduce_weighted(q2x_plan_t plan, int64_t n_elem, int p, cons
     check_leaf_off_kernel<<<(unsigned)((n_leaves + 1 + 255) / 256), 256, 0, plan->stream>>>(leaf_off, n_leaves, n_elem,
                                                                                            plan->d_err);
     const int warps = 8;
-    const int64_t units = n_leaves * (int64_t)((np + 31) / 32);
+    const int64_t units = n_leaves * (int64_t)((np + 31) / 32);  // (leaf, 32-column group) warps
     const unsigned grid = (unsigned)((units + warps - 1) / warps);
     switch (n_w) {
         case 1:
