@@ -147,17 +147,22 @@ __global__ void q2x_nearfield_faces(const NearArgs a, Face* faces)
     } else if (a.kind == 1) {
         make_face(X[0], X[1], X[2], F);
     } else {
+        // faces opposite vertex 0..3, outward when det[x1-x0, x2-x0, x3-x0] > 0
         const int T[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
         V3 p0 = X[T[f][0]], p1 = X[T[f][1]], p2 = X[T[f][2]];
-        const V3 c = scale(V3{X[0].x + X[1].x + X[2].x + X[3].x, X[0].y + X[1].y + X[2].y + X[3].y,
-                              X[0].z + X[1].z + X[2].z + X[3].z},
-                           0.25);
-        if (dot(cross(sub(p1, p0), sub(p2, p0)), sub(p0, c)) < 0.0) {  // orient outward
-            const V3 tmp = p1;
-            p1 = p2;
-            p2 = tmp;
+        const V3 e1 = sub(X[1], X[0]), e2 = sub(X[2], X[0]), e3 = sub(X[3], X[0]);
+        const double det = dot(e1, cross(e2, e3));
+        const double scale3 = sqrt(dot(e1, e1) * dot(e2, e2) * dot(e3, e3));
+        if (!(fabs(det) > NF_SNAP * 4.0 * scale3)) {
+            F = Face{};  // zero volume (to rounding): no potential, and no outward side to orient
+        } else {
+            if (det < 0.0) {  // negatively ordered vertices: every face flips
+                const V3 tmp = p1;
+                p1 = p2;
+                p2 = tmp;
+            }
+            make_face(p0, p1, p2, F);
         }
-        make_face(p0, p1, p2, F);
     }
     faces[i] = F;
 }
