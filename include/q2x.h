@@ -363,7 +363,7 @@ q2x_status q2x_evaluate_curl(q2x_plan_t plan, int p, int64_t n_exp, const double
  *               sigma[e] / (4 pi) * int_e n.(r_t - y)/|r_t - y|^3 dS   (layer 1,
  *               triangles: the double-layer kernel, a signed solid angle)
  * by the closed forms of Sec. 4.1 (Eqs. (num1)-(num3) for segments, the
- * edge-sum form for flat triangles, the divergence-theorem face sum of
+ * edge-sum form of Eq. (num5) for flat triangles, the divergence-theorem face sum of
  * Eqs. (num7)-(num8) for tetrahedra).  kind 0 segment, 1 triangle, 2
  * tetrahedron; vxyz, idx, sigma (per element) as q2x_segments/-triangles/
  * -tetra; tgt double[3 * n_tgt] SoA; tgt_off int64[n_tgt + 1] CSR into the

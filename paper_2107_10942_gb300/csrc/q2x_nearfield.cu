@@ -2,7 +2,7 @@
 // target points (the near field next to the expansions; Sec. 4.1's closed
 // forms as kernels):
 //   segment:      int 1/|r - y| dl = log((R_b + s_b) / (R_a + s_a))     (Eqs. (num1)-(num3))
-//   triangle:     int 1/|r - y| dS = sum_edges t_i log((R+ + s+)/(R- + s-)) - h Omega
+//   triangle:     int 1/|r - y| dS = sum_edges t_i log((R+ + s+)/(R- + s-)) - h Omega  (Eq. (num5))
 //   triangle, double layer: int n.(r - y)/|r - y|^3 dS = Omega, the signed solid angle
 //   tetrahedron:  int 1/|r - y| dV = -1/2 sum_faces h_j int_face 1/|r - y| dS  (Eqs. (num7)-(num8))
 // with, per triangle edge i (n the unit normal, m_i the outward in-plane edge
