@@ -175,16 +175,16 @@ __global__ void rho_bits_to_double(const int* bits, double* rho, int64_t n)
     if (L < n) rho[L] = (double)__int_as_float(bits[L]);
 }
 
-// segmented sum of per-element rows: one warp per (leaf, group of 32
-// columns), one column per lane, eight rows in flight per step; every column
-// is summed in element order (deterministic, the same order as a plain loop)
+// segmented sum of per-element rows: one thread per (leaf, column), eight
+// rows in flight per step; every column is summed in element order
+// (deterministic, the same order as a plain loop)
 __global__ void leaf_reduce_kernel(const double* __restrict__ elem, int np, int64_t n_elem,
                                    int64_t n_leaves, const int64_t* __restrict__ off, double* coef,
                                    int accumulate)
 {
     constexpr int U = 8;
-    // one thread per (leaf, column), leaves' columns back to back, so that a
-    // warp is full even where a leaf's last columns do not fill one
+    // the leaves' columns back to back, so that a warp is full even where a
+    // leaf's last columns do not fill one
     const int64_t unit = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t L = unit / np;
     if (L >= n_leaves) return;
