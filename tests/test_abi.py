@@ -76,3 +76,21 @@ def test_null_plan_rejected_by_every_compute_entry(so):
     for required in ("q2x_nearfield", "q2x_segments_vector", "q2x_leaf_reduce_weighted", "q2x_translate",
                      "q2x_evaluate", "q2x_evaluate_curl", "q2x_galerkin_triangles"):
         assert required in checked
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/q2x.h is a C header: a C99 translation unit that takes the
+    address of every declared function compiles without warnings."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = declared_functions()
+    src = tmp_path / "abi_check.c"
+    src.write_text('#include "q2x.h"\n#include <stddef.h>\nvoid* q2x_abi_table[] = {\n' +
+                   "".join("    (void*)&%s,\n" % n for n in names) + "    NULL\n};\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-Wno-pedantic",
+                        "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "abi_check.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
