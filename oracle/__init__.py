@@ -63,9 +63,10 @@ def lib():
             L.oracle_moments.argtypes = [i, i, i, i, i, i, i64, p, i64, p, p, i64, p, p, p, p, i]
             L.oracle_moments_cs.argtypes = [i, i, i, i, i, i64, p, p, i64, p, p, p, p, p, i]
             L.oracle_farfield.argtypes = [i, p, p, i64, p, p, p]
+            L.oracle_potential.argtypes = [i, i, i, i64, p, i64, p, p, i64, i64, i64, p, p, i]
             L.oracle_max_threads.argtypes = []
             for f in (L.oracle_gauss_legendre, L.oracle_rnm, L.oracle_snm, L.oracle_moments,
-                      L.oracle_moments_cs, L.oracle_farfield, L.oracle_max_threads):
+                      L.oracle_moments_cs, L.oracle_farfield, L.oracle_potential, L.oracle_max_threads):
                 f.restype = ctypes.c_int
             _LIB = L
     return _LIB
@@ -164,6 +165,26 @@ def moments_cs(kind, vre, vim, idx, sigma, elem_c, p, density=0, norm=NORM_COEFF
     if rc:
         raise ValueError("oracle_moments_cs failed: %d" % rc)
     return ore + 1j * oim
+
+
+def potential(kind, vxyz, idx, sigma, tgt, e0=0, e1=None, density=0, nq=12, nthreads=0) -> np.ndarray:
+    """Single-layer potential (1/4pi) sum_e int_e sigma / |r - y| of the
+    elements [e0, e1) at targets tgt (N, 3), by collapsed Gauss product rules
+    with nq nodes per direction (for targets well separated from the
+    elements; near targets need ``oracle.nearfield``)."""
+    k = KIND[kind] if isinstance(kind, str) else int(kind)
+    vxyz = _f64(vxyz)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    sigma = _f64(sigma)
+    tgt = _f64(np.atleast_2d(tgt))
+    n_elem = idx.shape[1]
+    e1 = n_elem if e1 is None else int(e1)
+    out = np.zeros(tgt.shape[0])
+    rc = lib().oracle_potential(k, int(density), int(nq), vxyz.shape[1], _ptr(vxyz), n_elem, _ptr(idx),
+                                _ptr(sigma), int(e0), e1, tgt.shape[0], _ptr(tgt), _ptr(out), nthreads)
+    if rc:
+        raise ValueError("oracle_potential failed: %d" % rc)
+    return out
 
 
 def farfield(coef, c, pts, p) -> np.ndarray:

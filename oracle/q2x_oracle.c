@@ -250,6 +250,85 @@ int oracle_moments_cs(int kind, int density, int norm, int p, int nq, int64_t n_
     return status;
 }
 
+/* Single-layer potential of the elements [e0, e1) at targets r (AoS 3 x n_tgt):
+ *   out[i] = (1/4pi) sum_e int_e sigma(y) / |r_i - y| dmu(y)
+ * (the potential that the coefficients of Eq. (st4) expand, Eq. (bas3)), by
+ * the collapsed Gauss-Legendre product rules of element_moments with nq
+ * nodes per direction: accurate to rounding for targets well separated from
+ * the elements, where the integrand is analytic on the element (near targets
+ * need the graded rules of nearfield.py).  Density as in oracle_moments
+ * (constant per element, or linear per vertex for triangles). */
+int oracle_potential(int kind, int density, int nq, int64_t n_vert, const double* vxyz, int64_t n_elem,
+                     const int32_t* idx, const double* sigma, int64_t e0, int64_t e1, int64_t n_tgt,
+                     const double* tgt, double* out, int nthreads)
+{
+    if (kind < 0 || kind > 2 || nq < 1 || nq > ORACLE_NQMAX || e0 < 0 || e1 > n_elem || e0 > e1) return -1;
+    if (density == 1 && kind != 1) return -3;
+    double gx[ORACLE_NQMAX], gw[ORACLE_NQMAX];
+    oracle_gauss_legendre(nq, gx, gw);
+    int nv = nvert_of(kind);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n_tgt; ++i) {
+        const double* r = tgt + 3 * i;
+        double acc = 0.0, comp = 0.0;
+        for (int64_t e = e0; e < e1; ++e) {
+            double X[12], sg[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < nv; ++k) {
+                int64_t vk = idx[(int64_t)k * n_elem + e];
+                for (int d = 0; d < 3; ++d) X[3 * k + d] = vxyz[(int64_t)d * n_vert + vk];
+                if (density == 1) sg[k] = sigma[vk];
+            }
+            if (density == 0) sg[0] = sigma[e];
+            double Ru[3], Rv[3], Rw[3];
+            for (int d = 0; d < 3; ++d) {
+                Ru[d] = X[3 + d] - X[d];
+                Rv[d] = (kind >= 1) ? X[6 + d] - X[d] : 0.0;
+                Rw[d] = (kind >= 2) ? X[9 + d] - X[d] : 0.0;
+            }
+            double J;
+            double cr[3] = {Ru[1] * Rv[2] - Ru[2] * Rv[1], Ru[2] * Rv[0] - Ru[0] * Rv[2],
+                            Ru[0] * Rv[1] - Ru[1] * Rv[0]};
+            if (kind == 0)
+                J = sqrt(Ru[0] * Ru[0] + Ru[1] * Ru[1] + Ru[2] * Ru[2]);
+            else if (kind == 1)
+                J = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+            else
+                J = fabs(cr[0] * Rw[0] + cr[1] * Rw[1] + cr[2] * Rw[2]);
+            int ns = nq, nt = (kind >= 1) ? nq : 1, nr = (kind >= 2) ? nq : 1;
+            double s = 0.0;
+            for (int is = 0; is < ns; ++is)
+                for (int it = 0; it < nt; ++it)
+                    for (int ir = 0; ir < nr; ++ir) {
+                        double u = gx[is], v = 0.0, w = 0.0, wt = gw[is];
+                        if (kind == 1) {
+                            v = (1.0 - u) * gx[it];
+                            wt *= gw[it] * (1.0 - u);
+                        } else if (kind == 2) {
+                            v = (1.0 - u) * gx[it];
+                            w = (1.0 - u) * (1.0 - gx[it]) * gx[ir];
+                            wt *= gw[it] * gw[ir] * (1.0 - u) * (1.0 - u) * (1.0 - gx[it]);
+                        }
+                        double dens = (density == 1) ? sg[0] * (1.0 - u - v) + sg[1] * u + sg[2] * v : sg[0];
+                        double dx = X[0] + Ru[0] * u + Rv[0] * v + Rw[0] * w - r[0];
+                        double dy = X[1] + Ru[1] * u + Rv[1] * v + Rw[1] * w - r[1];
+                        double dz = X[2] + Ru[2] * u + Rv[2] * v + Rw[2] * w - r[2];
+                        s += wt * dens / sqrt(dx * dx + dy * dy + dz * dz);
+                    }
+            double term = s * J / (4.0 * M_PI);
+            /* Neumaier summation over the elements */
+            double t = acc + term;
+            if (fabs(acc) >= fabs(term))
+                comp += (acc - t) + term;
+            else
+                comp += (term - t) + acc;
+            acc = t;
+        }
+        out[i] = acc + comp;
+    }
+    return 0;
+}
+
 /* Far-field series of Eq. (st4)/(bas3): phi(r) = sum_{n<=p} sum_m F_n^m
  * S_n^m(r - c) for packed COEFF-normalised coefficients F (the imaginary parts
  * of negative orders follow from F_n^{-m} = (-1)^m conj(F_n^m), Eq. (bas2.1)).
