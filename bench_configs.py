@@ -2,8 +2,6 @@
 
   icosphere-L3      1280 triangles of the level-3 icosphere, one expansion
                     about the origin, p = 10, FP64 (latency-bound)
-  sphere-L9-const   level-9 perturbed sphere, 5,242,880 triangles, constant
-                    density, depth-7 octree, p = 16: FP32-mixed vs FP64
   mixed-ball        2M filament segments + 4M sphere triangles + 1M tetrahedra
                     in the unit ball, adaptive octree (<= 2000 per leaf),
                     p_leaf ~ U{8..20}: one CUDA-graph replay of the batch (FP32)
@@ -27,6 +25,9 @@ import workloads as W
 from bench import METRIC, UNIT, ClockSampler, L2_FLUSH_BYTES
 
 LINES = []
+# filled by run(): measured FP64 / FP32 FMA peaks (flop/s) of this device
+PEAKS = {}
+PEAK_SOURCE = "measured in this run (q2x_alu_peak_probe, FMA chains on every SM, CUDA events)"
 
 
 def _norm_err(test, ref, rho, p, layer=0):
@@ -53,6 +54,7 @@ def _time(fn, steps, warmup, flush, stream):
     clk = ClockSampler()
     clk.start()
     ms = []
+    t0 = time.time()
     for k in range(steps):
         flush.fill_(float(k))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -61,7 +63,9 @@ def _time(fn, steps, warmup, flush, stream):
         b.record(stream)
         ms.append((a, b))
     torch.cuda.synchronize()
-    CLOCKS.update(clk.stop())
+    clk.window("timed", t0, time.time())
+    clk.stop()
+    CLOCKS.update(clk.summary())
     return sum(x.elapsed_time(y) for x, y in ms) / steps
 
 
@@ -69,66 +73,6 @@ def _emit(line):
     line["clocks"] = dict(CLOCKS)
     line["config"]["l2"] = "flushed between timed steps (256 MiB write)"
     print(json.dumps(line), flush=True)
-
-
-def run_sphere_l9(args, dev):
-    import paper_2107_10942_gb300 as q
-    from paper_2107_10942_gb300.q2x import problem_to_device
-    from paper_2107_10942_gb300.roofline import PEAK_FP32_FLOPS, PEAK_FP64_FLOPS, element_flops
-    prob = W.cfg_sphere_const(level=9, depth=7, p=16)
-    d = problem_to_device({k: v for k, v in prob.items() if hasattr(v, "shape")}, dev)
-    p = 16
-    n_elem = prob["idx"].shape[1]
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-    res, outs = {}, {}
-    for prec in ("fp64", "fp32"):
-        plan = q.Plan(p, precision=prec)
-        coef = torch.empty((prob["leaf_c"].shape[1], (p + 1) ** 2), dtype=torch.float64, device=dev)
-        fn = lambda: plan.triangles(d["vxyz"], d["idx"], d["sigma"], d["leaf_off"], d["leaf_c"], d["leaf_rho"],
-                                    None, coef_single=coef)
-        ms = _time(fn, args.steps, args.warmup, flush, stream)
-        plan.set_kernel_timing(True)
-        plan.kernel_timing()
-        _time(fn, 3, 0, flush, stream)
-        kms, kn = plan.kernel_timing()
-        plan.sync()
-        res[prec] = (ms, kms / kn)
-        outs[prec] = coef.cpu().numpy()
-    flops = element_flops("triangle", "const", ("single",), p) * n_elem
-    import oracle as orc
-    rng = np.random.default_rng(3)
-    nl = prob["leaf_c"].shape[1]
-    pick = np.sort(rng.choice(nl, size=24, replace=False))
-    off = prob["leaf_off"]
-    ref = []
-    t0 = time.perf_counter()
-    ne = 0
-    for L in pick:
-        idx = np.ascontiguousarray(prob["idx"][:, off[L]:off[L + 1]])
-        ne += idx.shape[1]
-        ref.append(orc.moments("triangle", prob["vxyz"], idx, prob["sigma"][off[L]:off[L + 1]], p,
-                               leaf_off=np.array([0, idx.shape[1]]), leaf_c=prob["leaf_c"][:, L:L + 1])[0])
-    dt = time.perf_counter() - t0
-    ref = np.array(ref)
-    errs = {prec: _norm_err(outs[prec][pick], ref, prob["leaf_rho"][pick], p) for prec in outs}
-    per_step = n_elem * (p + 1) ** 2
-    _emit({"metric": METRIC, "value": per_step / (res["fp64"][0] * 1e-3), "unit": UNIT, "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["fp64"][0], "higher_is_better": True,
-           "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "sphere-L9-const: %d triangles, depth 7 (%d leaves), p=16, single layer" % (n_elem, nl)},
-           "roofline": {"bound": "alu", "achieved": flops / (res["fp64"][1] * 1e-3) / 1e12,
-                        "peak": PEAK_FP64_FLOPS / 1e12, "unit": "TFLOP/s",
-                        "frac": flops / (res["fp64"][1] * 1e-3) / PEAK_FP64_FLOPS, "kernel_ms": res["fp64"][1]},
-           "fp32_mixed": {"value": per_step / (res["fp32"][0] * 1e-3), "ms_per_step": res["fp32"][0],
-                          "speedup_vs_fp64": res["fp64"][0] / res["fp32"][0],
-                          "roofline": {"bound": "alu", "achieved": flops / (res["fp32"][1] * 1e-3) / 1e12,
-                                       "peak": PEAK_FP32_FLOPS / 1e12, "unit": "TFLOP/s",
-                                       "frac": flops / (res["fp32"][1] * 1e-3) / PEAK_FP32_FLOPS,
-                                       "kernel_ms": res["fp32"][1]}},
-           "errors_vs_oracle": errs,
-           "cpu_baseline": {"value": ne * (p + 1) ** 2 / dt, "unit": UNIT, "kind": "oracle",
-                            "cores": orc.max_threads(), "sample": "%d triangles in 24 sampled leaves" % ne}})
 
 
 def run_mixed_ball(args, dev):
@@ -170,7 +114,7 @@ def run_mixed_ball(args, dev):
     dt = time.perf_counter() - t0
     err = _norm_err(got[pick], ref, m["leaf_rho"][pick], m["p"])
     info = b.info()
-    from paper_2107_10942_gb300.roofline import PEAK_FP32_FLOPS, element_flops
+    from paper_2107_10942_gb300.roofline import element_flops
     kind_flops = {"segment": ("segment", "const"), "triangle": ("triangle", "const"), "tetra": ("tetra", "const")}
     flops = 0.0
     for k, dd in m["kinds"].items():
@@ -187,8 +131,8 @@ def run_mixed_ball(args, dev):
                                                              [m["leaf_c"].shape[1]]),
                       "tiles": info["tiles"], "tile_elems": info["tile_elems"],
                       "launch": "one CUDA-graph replay (counter reset, persistent kernel, combine)"},
-           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP32_FLOPS / 1e12,
-                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP32_FLOPS,
+           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAKS["fp32"] / 1e12,
+                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAKS["fp32"],
                         "note": "whole graph replay (reset + persistent kernel + combine) as the duration"},
            "errors_vs_oracle": {"fp32": err, "sampled_leaves": len(pick)},
            "cpu_baseline": {"value": float(np.sum(n_per_leaf[pick] * (lpn[pick] + 1) ** 2)) / dt, "unit": UNIT,
@@ -222,15 +166,15 @@ def run_adjoint(args, dev):
     rel_v = float(np.max(np.abs(gv32 - gv64)) / np.max(np.abs(gv64)))
     rel_s = float(np.max(np.abs(gs32 - gs64)) / np.max(np.abs(gs64)))
     per_step = n_elem * (p + 1) ** 2
-    from paper_2107_10942_gb300.roofline import PEAK_FP32_FLOPS, element_flops, vjp_flops
+    from paper_2107_10942_gb300.roofline import element_flops, vjp_flops
     flops = float(element_flops("triangle", "const", ("single",), p) + vjp_flops(p)) * n_elem
     _emit({"metric": METRIC + " (forward + adjoint)", "value": per_step / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "dtype": "f32-mixed forward, f32 per element + f64 accumulation backward", "data": "synthetic",
            "config": {"workload": "sphere-L8-adjoint: %d triangles, depth 6, p=12, single layer, "
                                   "loss = sum(G * coef), G ~ N(0,1)" % n_elem},
-           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP32_FLOPS / 1e12,
-                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP32_FLOPS,
+           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAKS["fp32"] / 1e12,
+                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAKS["fp32"],
                         "flops_per_element": flops / n_elem,
                         "note": "whole step (forward kernel + adjoint kernels + autograd glue) against the FP32 peak"},
            "errors_vs_fp64_adjoint": {"grad_vertices": rel_v, "grad_sigma": rel_s}})
@@ -286,7 +230,6 @@ def translate_macs(p):
 
 def run_upward(args, dev):
     import paper_2107_10942_gb300 as q
-    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS
     from paper_2107_10942_gb300.upward import Upward
     import oracle as orc
     p, depth = 12, 5
@@ -318,8 +261,8 @@ def run_upward(args, dev):
            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "upward pass of the level-7 sphere's depth-5 leaves (%d leaves, %d translations, "
                                   "5 levels, one CUDA graph replay), p=12, FP64" % (prob["leaf_c"].shape[1], n_tr)},
-           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
-                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP64_FLOPS,
+           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAKS["fp64"] / 1e12,
+                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAKS["fp64"],
                         "flops_per_translation": 8 * translate_macs(p)},
            "errors_vs_oracle": {"root_vs_quadrature": err},
            "cpu_baseline": {"value": None, "note": "oracle quadrature of the root expansion over all %d triangles: "
@@ -340,7 +283,6 @@ def eval_flops(p):
 
 def run_farfield(args, dev):
     import paper_2107_10942_gb300 as q
-    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS
     from paper_2107_10942_gb300.upward import Upward
     import oracle as orc
     p, depth, n_tgt = 12, 5, 1 << 20
@@ -373,19 +315,19 @@ def run_farfield(args, dev):
            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "root expansion of the level-7 sphere (p=12, from Q2X + upward pass) at %d targets "
                                   "on the radius-3 sphere" % n_tgt},
-           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
-                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP64_FLOPS,
+           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAKS["fp64"] / 1e12,
+                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAKS["fp64"],
                         "flops_per_evaluation": eval_flops(p),
                         "executed": {"flops_per_evaluation": EVAL_EXECUTED_FLOPS,
-                                     "frac": EVAL_EXECUTED_FLOPS * n_tgt / (ms * 1e-3) / PEAK_FP64_FLOPS,
-                                     "source": "ncu DFMA/DADD/DMUL counts, "
-                                               "profiles/q2x_evaluate_kernel_far-field-p12.md"}},
+                                     "frac": EVAL_EXECUTED_FLOPS * n_tgt / (ms * 1e-3) / PEAKS["fp64"],
+                                     "source": "ncu DFMA/DADD/DMUL counts of one capture of this "
+                                               "kernel on this workload"}},
            "errors_vs_oracle": {"series": err, "sampled_targets": 64}})
 
 
 def run_galerkin(args, dev):
     import paper_2107_10942_gb300 as q
-    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS, element_flops
+    from paper_2107_10942_gb300.roofline import element_flops
     import oracle as orc
     p, depth = 12, 5
     prob = W.cfg_sphere_linear(level=7, depth=depth, p=p)
@@ -418,14 +360,14 @@ def run_galerkin(args, dev):
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "the level-7 sphere's %d triangles against random local expansions of its %d "
                                   "depth-5 leaves, p=12, single layer" % (n_elem, nl)},
-           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
-                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP64_FLOPS},
+           "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAKS["fp64"] / 1e12,
+                        "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAKS["fp64"]},
            "errors_vs_oracle": {"relative_to_sum_of_terms": err, "sampled_elements": 200}})
 
 
 def run_biot_savart(args, dev):
     import paper_2107_10942_gb300 as q
-    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS, level_flops
+    from paper_2107_10942_gb300.roofline import level_flops
     from paper_2107_10942_gb300.upward import Upward
     p = 12
     m = W.cfg_mixed_ball()
@@ -466,8 +408,8 @@ def run_biot_savart(args, dev):
                                   "adaptive leaves, p=12 (one recursion pass for the three components)" % (n_elem,
                                                                                            m["leaf_c"].shape[1])},
            "roofline": {"bound": "alu", "achieved": flops / (ms_q2x * 1e-3) / 1e12,
-                        "peak": PEAK_FP64_FLOPS / 1e12, "unit": "TFLOP/s",
-                        "frac": flops / (ms_q2x * 1e-3) / PEAK_FP64_FLOPS},
+                        "peak": PEAKS["fp64"] / 1e12, "unit": "TFLOP/s",
+                        "frac": flops / (ms_q2x * 1e-3) / PEAKS["fp64"]},
            "curl_evaluation": {"targets": n_tgt, "ms": ms_curl, "value": n_tgt / (ms_curl * 1e-3),
                                "unit": "H evaluations/s (root expansion, p=12, radius 2)"}})
 
@@ -518,7 +460,8 @@ def run_leaf_reduce(args, dev):
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                         "peak_source": src, "bytes_per_launch": bytes_,
                         "traffic": 444732928 + 6349568,
-                        "traffic_source": "ncu dram__bytes_read/write, profiles/leaf_reduce_kernel_sphere-L7-p12.md"},
+                        "traffic_source": "ncu dram__bytes_read/write of one capture of this kernel on this "
+                                          "workload"},
            "errors_vs_oracle": {"max_abs_vs_sequential_sum": err, "sampled_leaves": 20}})
 
 
@@ -537,7 +480,6 @@ NEARFIELD_EXECUTED_FLOPS_PER_PAIR = (2 * 92.309745 + 33.237194 + 37.074234) * 59
 
 def run_nearfield(args, dev):
     import paper_2107_10942_gb300 as q
-    from paper_2107_10942_gb300.roofline import PEAK_FP64_FLOPS
     from oracle import nearfield as onf
     p = 12
     prob = W.cfg_sphere_linear(level=7, depth=5, p=p)
@@ -575,15 +517,15 @@ def run_nearfield(args, dev):
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "collocation at the centroids of the level-7 sphere's %d triangles, each against "
                                   "every triangle of its depth-5 leaf: %d pairs, single layer" % (n_elem, pairs)},
-           "roofline": {"bound": "alu", "achieved": ops / (ms * 1e-3) / 1e12, "peak": PEAK_FP64_FLOPS / 1e12,
-                        "unit": "TFLOP/s", "frac": ops / (ms * 1e-3) / PEAK_FP64_FLOPS,
+           "roofline": {"bound": "alu", "achieved": ops / (ms * 1e-3) / 1e12, "peak": PEAKS["fp64"] / 1e12,
+                        "unit": "TFLOP/s", "frac": ops / (ms * 1e-3) / PEAKS["fp64"],
                         "ops_per_pair": NEARFIELD_OPS_PER_PAIR,
                         "note": "sqrt, division, log and atan2 count as one operation each: a lower bound",
                         "executed": {"flops_per_pair": NEARFIELD_EXECUTED_FLOPS_PER_PAIR,
                                      "frac": NEARFIELD_EXECUTED_FLOPS_PER_PAIR * pairs / (ms * 1e-3)
-                                     / PEAK_FP64_FLOPS,
-                                     "source": "ncu DFMA/DADD/DMUL counts, "
-                                               "profiles/q2x_nearfield_kernel_sphere-L7-collocation.md"}},
+                                     / PEAKS["fp64"],
+                                     "source": "ncu DFMA/DADD/DMUL counts of one capture of this "
+                                               "kernel on this workload"}},
            "errors_vs_oracle": {"graded_quadrature": err, "sampled_targets": len(pick)}})
 
 
@@ -597,7 +539,13 @@ def run(args):
     torch.cuda.set_device(dev)
     from paper_2107_10942_gb300 import build
     build.build()
-    {"icosphere-L3": run_icosphere_l3, "sphere-L9-const": run_sphere_l9, "upward": run_upward,
+    # ALU peaks of this device, measured in this run (the roofline denominators)
+    from bench import measure_alu_peaks
+    pk = measure_alu_peaks(dev, 0.5)
+    PEAKS["fp64"] = pk["dfma"]["tflops"] * 1e12
+    PEAKS["fp32"] = max(pk["ffma"]["tflops"], pk["ffma2"]["tflops"]) * 1e12
+    PEAKS["measured"] = pk
+    {"icosphere-L3": run_icosphere_l3, "upward": run_upward,
      "far-field": run_farfield, "galerkin": run_galerkin, "biot-savart": run_biot_savart,
      "leaf-reduce": run_leaf_reduce, "near-field": run_nearfield, "mixed-ball": run_mixed_ball,
      "sphere-L8-adjoint": run_adjoint}[args.config](args, dev)

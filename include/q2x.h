@@ -180,18 +180,20 @@ q2x_status q2x_tetra(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const doub
  * Scratch: the partial sums of leaves that straddle warp ranges live in one
  * file-scope device array of Q2X_NOALLOC_SCRATCH_BYTES (16 MiB), which every
  * GPU that loads the library holds until the process exits.  Each warp range
- * covers Q2X_NOALLOC_RANGE elements and needs 4 (p_max+1)^2 s bytes
- * (s = 8 for FP64, 4 for FP32-mixed), so the call accepts
- *   n_elem <= Q2X_NOALLOC_RANGE * floor(Q2X_NOALLOC_SCRATCH_BYTES / (4 (p_max+1)^2 s))
- * (e.g. 794,112 triangles at p_max = 12 in FP64) and returns Q2X_ERR_RANGE
- * above that, having launched nothing.
+ * covers Q2X_NOALLOC_RANGE elements and needs 4 (p_max+1)^2 8 bytes (FP64
+ * partial sums in both precisions), so the call accepts
+ *   n_elem <= Q2X_NOALLOC_RANGE * floor(Q2X_NOALLOC_SCRATCH_BYTES / (32 (p_max+1)^2))
+ * (e.g. 794,112 triangles at p_max = 12) and returns Q2X_ERR_RANGE above
+ * that, having launched nothing.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current) and caches it: make that
- * first call before any stream capture.  Every call shares the array; calls
+ * first call before any stream capture.  cuda_stream must belong to the
+ * current device (Q2X_ERR_ARG otherwise).  Every call shares the array; calls
  * that overlap on the GPU race on it and on the device error word.  Device-side
- * input checks are not reported by this entry point (invalid elements
- * contribute zero).  Asynchronous on cuda_stream; no allocation, no
- * synchronisation. */
+ * input checks are not reported by this entry point: an invalid element
+ * contributes zero, and a leaf_off that is not non-decreasing from 0 to n_elem
+ * gives undefined coefficients (every memory access stays in bounds).
+ * Asynchronous on cuda_stream; no allocation, no synchronisation. */
 #define Q2X_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define Q2X_NOALLOC_RANGE 256
 q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precision precision,
@@ -448,6 +450,24 @@ q2x_status q2x_leaf_reduce_weighted(q2x_plan_t plan, int64_t n_elem, int p, cons
                                     const double* w, int64_t w_stride, int64_t n_leaves,
                                     const int64_t* leaf_off, double* coef, int64_t coef_stride,
                                     int accumulate);
+
+/* ---- Measurement aid (no counterpart in the paper) ----------------------
+ * ALU peak probe: the element kernels are bound by the FP64 or FP32 FMA
+ * pipes, so their roofline divides by the FMA rate this device actually
+ * sustains.  One launch, asynchronous on cuda_stream (cudaStream_t, NULL =
+ * legacy default stream) of the current device, of 4 CTAs x 256 threads per
+ * SM, each thread running 8 independent chains x <- a x + b for iters steps
+ * (rounded up to a multiple of 16):
+ *   Q2X_PEAK_DFMA   FP64 fma            2 flops per FMA
+ *   Q2X_PEAK_FFMA   FP32 fma            2 flops per FMA
+ *   Q2X_PEAK_FFMA2  packed fma.rn.f32x2 4 flops per instruction
+ * *flops (host) receives the floating-point operations the launch performs;
+ * the caller times the launch with CUDA events on the same stream.
+ * sink: device double[1], written only if a chain sum takes a value it never
+ * takes (it keeps the chains live; nothing is stored in practice).
+ * Q2X_ERR_ARG for a bad kind, iters outside 1..2^40 or a NULL pointer. */
+typedef enum { Q2X_PEAK_DFMA = 0, Q2X_PEAK_FFMA = 1, Q2X_PEAK_FFMA2 = 2 } q2x_peak_kind;
+q2x_status q2x_alu_peak_probe(int kind, int64_t iters, double* sink, void* cuda_stream, double* flops);
 
 #ifdef __cplusplus
 }

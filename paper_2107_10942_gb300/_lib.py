@@ -49,6 +49,7 @@ _SIGNATURES = {
     "q2x_batch_destroy": [_p],
     "q2x_batch_info": [_p, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i)],
     "q2x_batch_tune": [_p, _p, _p, _i, _i, _c.POINTER(_i), _c.POINTER(_c.c_float)],
+    "q2x_alu_peak_probe": [_i, _i64, _p, _p, _c.POINTER(_c.c_double)],
 }
 
 

@@ -381,7 +381,6 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     const int bin = bin_index(plan->p_max);
     if (bin < 0) return fail(plan, Q2X_ERR_RANGE, "p_max %d above %d", plan->p_max, Q2X_P_MAX);
     const KernelEntry& ke = kTable[prec][combo][bin];
-    const size_t elt = prec ? sizeof(float) : sizeof(double);
     const size_t smem = q2x::WARPS_PER_CTA *
                         (prec ? q2x::warp_smem_bytes<float>(np) : q2x::warp_smem_bytes<double>(np));
 
@@ -400,7 +399,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
 
     // workspace: slots, then per-leaf scale (FP32 without leaf_rho)
     const bool need_rho = prec == 1 && leaf_rho == nullptr;
-    const size_t slot_bytes = align_up(elt * (size_t)n_ranges * 2 * 2 * np, 256);
+    const size_t slot_bytes = align_up(sizeof(double) * (size_t)n_ranges * 2 * 2 * np, 256);  // FP64 partials
     const size_t rho_bytes = need_rho ? align_up(sizeof(double) * (size_t)n_leaves, 256) : 0;
     const size_t bits_bytes = need_rho ? align_up(sizeof(int) * (size_t)n_leaves, 256) : 0;
     q2x_status st = ensure_ws(plan, slot_bytes + rho_bytes + bits_bytes);
@@ -445,7 +444,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     a.norm = plan->norm;
     a.T = T;
     a.n_ranges = n_ranges;
-    a.slots = ws;
+    a.slots = reinterpret_cast<double*>(ws);
     a.err = plan->d_err;
     a.raw = raw;
 
@@ -468,10 +467,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
         const int d_out = (kind == q2x::KIND_SEG) ? 1 : (kind == q2x::KIND_TET) ? 3 : (dens == Q2X_DENSITY_LINEAR ? 3 : 2);
         const int64_t nw = n_ranges - 1;
         const int fgrid = (int)((nw + 3) / 4);
-        if (prec)
-            q2x::q2x_fixup_kernel<float><<<fgrid, 128, 0, plan->stream>>>(a, kind + 1, d_out, d_out - 1);
-        else
-            q2x::q2x_fixup_kernel<double><<<fgrid, 128, 0, plan->stream>>>(a, kind + 1, d_out, d_out - 1);
+        q2x::q2x_fixup_kernel<<<fgrid, 128, 0, plan->stream>>>(a, kind + 1, d_out, d_out - 1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(plan, e, "fixup kernel launch");
         plan->launches += 1;
@@ -620,10 +616,9 @@ q2x_status q2x_reserve(q2x_plan_t plan, int64_t n_elem, int64_t n_leaves)
     if (!plan || n_elem < 0 || n_leaves < 0) return fail(plan, Q2X_ERR_ARG, "bad reserve arguments");
     cudaSetDevice(plan->device);
     const int np = (plan->p_max + 1) * (plan->p_max + 1);
-    const size_t elt = plan->prec ? sizeof(float) : sizeof(double);
-    // worst case: one range per 32 elements
+    // worst case: one range per 32 elements; FP64 partials in both precisions
     const int64_t n_ranges = (n_elem + 31) / 32;
-    const size_t bytes = align_up(elt * (size_t)n_ranges * 2 * 2 * np, 256) +
+    const size_t bytes = align_up(sizeof(double) * (size_t)n_ranges * 2 * 2 * np, 256) +
                          align_up(sizeof(double) * (size_t)n_leaves, 256) +
                          align_up(sizeof(int) * (size_t)n_leaves, 256);
     return ensure_ws(plan, bytes);

@@ -52,14 +52,17 @@ struct BatchArgs {
 
 constexpr int BATCH_WARPS = 4;
 
+// stage tile [CHUNK][LD] of T, then the tile's column sums [np_max] (LeafSum)
 template <typename T>
 __host__ __device__ constexpr size_t batch_warp_smem_bytes(int np_max)
 {
-    return (sizeof(T) * (size_t)(KCfg<T>::CHUNK * KCfg<T>::LD + np_max) + 127) / 128 * 128;
+    return (sizeof(T) * (size_t)(KCfg<T>::CHUNK * KCfg<T>::LD) + sizeof(LeafSum<T>) * (size_t)np_max + 127) /
+           128 * 128;
 }
 
 template <typename T, int P, int KIND, int DENS>
-__device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& t, T* tile, T* accb, int lane)
+__device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& t, T* tile, LeafSum<T>* accb,
+                                           int lane)
 {
     using C = Chain<KIND, DENS>;
     constexpr int LD = KCfg<T>::LD;
@@ -76,7 +79,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& 
                  cz = __ldg(b.leaf_c + 2 * b.n_leaves + L);
     if (!(finite_bits(cx) && finite_bits(cy) && finite_bits(cz))) errbits |= 2u;
     const int sexp = b.leaf_rho ? scale_exponent(__ldg(b.leaf_rho + L)) : 0;
-    for (int c = lane; c < np; c += 32) accb[c] = T(0);
+    for (int c = lane; c < np; c += 32) accb[c].zero();
     __syncwarp();
     if (pL >= 0) {
 #pragma unroll 1
@@ -88,7 +91,9 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& 
             load_frame<T, KIND, DENS>(K.vx, K.vy, K.vz, K.idx, K.sigma, K.n_elem, K.n_vert, e, active, cx, cy,
                                       cz, sexp, errbits, pl, F);
             run_chain<T, P, KIND, DENS, 1>(F, pL, tile, lane, [&](int c0, int ncols) {
-                for (int j = lane; j < ncols; j += 32) accb[c0 + j] += sum_rows32(tile + j * LD);
+                // each round's 32 rows summed pairwise, the rounds accumulated
+                // in a LeafSum (compensated in FP32)
+                for (int j = lane; j < ncols; j += 32) accb[c0 + j].add(sum_rows32(tile + j * LD));
             });
         }
     }
@@ -99,7 +104,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& 
 #pragma unroll 1
     for (int c = lane; c < np; c += 32) {
         double v = 0.0;
-        if (c < npl) v = finish_desc(accb[c], b.norm, col_desc(c), C::D_OUT, KIND + 1, sexp);
+        if (c < npl) v = finish_desc(accb[c].rounded(), b.norm, col_desc(c), C::D_OUT, KIND + 1, sexp);
         out[c] = v;
     }
     __syncwarp();
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, 2) q2x_batch_kernel(const Ba
     const int wib = threadIdx.x >> 5;
     unsigned char* wsm = smem_raw + (size_t)wib * batch_warp_smem_bytes<T>(b.np_max);
     T* tile = reinterpret_cast<T*>(wsm);
-    T* accb = tile + KCfg<T>::CHUNK * KCfg<T>::LD;
+    LeafSum<T>* accb = reinterpret_cast<LeafSum<T>*>(tile + KCfg<T>::CHUNK * KCfg<T>::LD);  // CHUNK LD sizeof(T) % 8 == 0
 #pragma unroll 1
     while (true) {
         unsigned long long ti = 0;

@@ -47,9 +47,12 @@
 // Scaled local frame: y' = (x - r*) / 2^s with 2^s >= rho_leaf, so |y'| <~ 1;
 // homogeneity of R_n^m (degree n) and the Jacobian (degree dim) give the factor
 // 2^{s (n + dim)} (double layer 2^{s (n + 1)}), applied exactly as an exponent
-// shift when the FP64 coefficient is formed.  In the FP32 path every FP64
-// quantity is handled with integer operations (exact splitting of the inputs,
-// exponent re-biasing of the outputs), so no FP64 arithmetic runs per moment.
+// shift when the FP64 coefficient is formed.  In the FP32 path the inputs are
+// split exactly into FP32 pairs with integer operations, the Jacobian and the
+// seed are formed in FP64 from the FP64 vertices (once per element), each
+// round's 32-row column sums are added into compensated FP32 leaf sums, and a
+// leaf's coefficients are re-biased exactly into FP64: no FP64 arithmetic runs
+// per moment or per round.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -102,7 +105,7 @@ struct ElemArgs {
     int norm;                 // 0 COEFF, 1 MOMENT
     int64_t T;                // elements per warp range, multiple of 32
     int64_t n_ranges;
-    void* slots;              // [n_ranges][2 slots][2 layers][np_max] accumulators
+    double* slots;            // [n_ranges][2 slots][2 layers][np_max] FP64 partial sums
     unsigned* err;
     int raw = 0;              // per-element mode: store the hat sums unfinished
 };
@@ -394,27 +397,12 @@ __device__ __forceinline__ int col_desc(int c)
     return (int)__ldg(&g_coltab.v[c]);
 }
 
-// final coefficient of column (n, m) from a sum acc:
-// acc * sign / (n+d)! (/ 4pi for COEFF) * 2^shift
+// final coefficient of column (n, m) (its descriptor from col_desc) from a
+// sum acc: acc * sign / (n+d)! (/ 4pi for COEFF) * 2^(s (n + shift_n0)), the
+// power of two being the leaf scale of the frame (exact).
 // FP32 sums: one FP32 multiply by the table significand (relative rounding
 // 2^-24), then the power of two is applied while re-biasing into FP64, so
-// tiny coefficients cannot underflow and no FP64 arithmetic is needed; this
-// runs once per flushed leaf column, not per moment.
-__device__ __forceinline__ double finish_value(float acc, int norm, int n, int m, int d, int shift)
-{
-    float v = acc * c_finish.mant[norm][n + d];
-    if (column_negative(norm, n, m)) v = -v;
-    return f32_scaled_to_f64(v, shift + c_finish.expo[norm][n + d]);
-}
-__device__ __forceinline__ double finish_value(double acc, int norm, int n, int m, int d, int shift)
-{
-    double cst = c_inv_fact_d[n + d];
-    if (norm == 0) cst *= INV_4PI;
-    if (column_negative(norm, n, m)) cst = -cst;
-    return acc * cst * pow2d(shift);
-}
-
-// the same from a column descriptor (col_desc): n and the sign from the table
+// tiny coefficients cannot underflow and no FP64 arithmetic is needed.
 __device__ __forceinline__ double finish_desc(float acc, int norm, int desc, int d, int shift_n0, int s)
 {
     const int n = desc & 31;
@@ -485,17 +473,50 @@ struct RangeCtx {
     int shift_n00, shift_n01;  // shift = s * (n + shift_n0 of the layer)
 };
 
+// Running sum of one column over a leaf's rounds.  FP32: compensated (each
+// round's 32-row partial is added by TwoSum and the rounding errors are
+// accumulated beside the sum), so the leaf sum keeps FP32 accuracy relative
+// to its own size however many rounds a leaf spans; all on the FP32 pipe.
+// FP64: a plain sum.  8 bytes either way.
+template <typename T>
+struct LeafSum;
+template <>
+struct LeafSum<float> {
+    float s, c;
+    __device__ __forceinline__ void zero() { s = c = 0.f; }
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = s + x;  // TwoSum: t + e = s + x exactly
+        const float bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
+        s = t;
+    }
+    __device__ __forceinline__ float rounded() const { return s + c; }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }  // exact
+};
+template <>
+struct LeafSum<double> {
+    double s;
+    __device__ __forceinline__ void zero() { s = 0.0; }
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double rounded() const { return s; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+static_assert(sizeof(LeafSum<float>) == 8 && sizeof(LeafSum<double>) == 8, "shared-memory layout assumes 8 bytes");
+
+// Flush a column's leaf sum: a complete leaf is finished and written; a leaf
+// that straddles the range goes to its FP64 slot partial.
 template <typename T>
 __device__ __forceinline__ void flush_value(const ElemArgs& a, const RangeCtx& rc, int ly, int c,
-                                            T acc, long long L, int info)
+                                            const LeafSum<T>& acc, long long L, int info)
 {
     if (info & 1) {
         const int desc = col_desc(c);
         double v = 0.0;
         if ((desc & 31) < ((info >> 1) & 63))  // n <= p_leaf
-            v = a.raw ? (double)acc
-                      : finish_desc(acc, a.norm, desc, ly ? rc.d_out1 : rc.d_out0, ly ? rc.shift_n01 : rc.shift_n00,
-                                    info >> 7);
+            v = a.raw ? acc.value()
+                      : finish_desc(acc.rounded(), a.norm, desc, ly ? rc.d_out1 : rc.d_out0,
+                                    ly ? rc.shift_n01 : rc.shift_n00, info >> 7);
         double* dst = a.coef[ly] + (int64_t)L * a.np_max + c;
         if (a.accumulate)
             *dst += v;
@@ -503,8 +524,7 @@ __device__ __forceinline__ void flush_value(const ElemArgs& a, const RangeCtx& r
             *dst = v;
     } else {
         const int slot = (L == rc.L_first) ? 0 : 1;
-        T* sl = reinterpret_cast<T*>(a.slots) + (((rc.w * 2 + slot) * 2 + ly) * (int64_t)a.np_max + c);
-        *sl = acc;
+        a.slots[((rc.w * 2 + slot) * 2 + ly) * (int64_t)a.np_max + c] = acc.value();
     }
 }
 
@@ -553,12 +573,12 @@ __device__ __forceinline__ T sum_rows32(const T* col)
 // g starts a new leaf, whose id and info are rowleaf[4g], rowinfo[4g]) are
 // summed and flushed in order.  The wanted layers' columns form one index
 // space; lane j owns indices j, j+32, ...; the open run's sum lives in accb
-// between chunks and rounds.  Per-element expansions (no leaves): row r is
-// the complete expansion of element rowleaf[r], finished directly.  All
-// control flow is warp-uniform.
+// between chunks and rounds (a LeafSum: compensated in FP32).  Per-element
+// expansions (no leaves): row r is the complete expansion of element
+// rowleaf[r], finished directly.  All control flow is warp-uniform.
 template <typename T>
 __device__ __forceinline__ void reduce_chunk(const ElemArgs& a, const RangeCtx& rc, const T* tile,
-                                             T* accb, const long long* rowleaf, const int* rowinfo,
+                                             LeafSum<T>* accb, const long long* rowleaf, const int* rowinfo,
                                              long long open_leaf, int open_info, unsigned gstart,
                                              int nrows, int c0, int ncols, bool want0, bool want1,
                                              bool per_elem)
@@ -582,7 +602,10 @@ __device__ __forceinline__ void reduce_chunk(const ElemArgs& a, const RangeCtx& 
             const int second = (tc >= ncols) ? 1 : 0;
             const int ly = want0 ? second : 1;
             const int j = tc - second * ncols;
-            flush_value<T>(a, rc, ly, c0 + j, tile[(ly * CH + j) * LD + r], rowleaf[r], rowinfo[r]);
+            LeafSum<T> one;
+            one.zero();
+            one.s = tile[(ly * CH + j) * LD + r];
+            flush_value<T>(a, rc, ly, c0 + j, one, rowleaf[r], rowinfo[r]);
             tc += 32;
             while (tc >= total) {
                 tc -= total;
@@ -599,9 +622,9 @@ __device__ __forceinline__ void reduce_chunk(const ElemArgs& a, const RangeCtx& 
         const int c = c0 + j;
         T s[8];
         group_sums(tile + (ly * CH + j) * LD, s);
-        T acc = accb[ly * a.np_max + c];
+        LeafSum<T> acc = accb[ly * a.np_max + c];
         if (gstart == 0) {
-            acc += ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+            acc.add(((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
         } else {
             long long L = open_leaf;
             int info = open_info;
@@ -610,15 +633,15 @@ __device__ __forceinline__ void reduce_chunk(const ElemArgs& a, const RangeCtx& 
             while (mask) {
                 const int r = __ffs(mask) - 1;
                 const int g1 = r >> 2;
-                acc += tree8(s, g0, g1);
+                acc.add(tree8(s, g0, g1));
                 flush_value<T>(a, rc, ly, c, acc, L, info);
-                acc = T(0);
+                acc.zero();
                 L = rowleaf[r];
                 info = rowinfo[r];
                 g0 = g1;
                 mask &= mask - 1;
             }
-            acc += tree8(s, g0, 8);
+            acc.add(tree8(s, g0, 8));
         }
         accb[ly * a.np_max + c] = acc;
     }
@@ -658,9 +681,12 @@ struct Chain<KIND_TET, DENS_CONST> {  // q (x2), j (x3), b (x4), a (x1)
 // the leaf centre (cx, cy, cz) and scale by 2^-sexp (FP32: from exact hi/lo
 // splits of the FP64 inputs), read the densities, and form the stencil
 // coefficients of every level of the chain, the unit normal (triangles) and
-// the seed J * density (linear density: J).  An inactive lane, a bad vertex
-// index or a non-finite input gives an all-zero frame and pL = -1; errbits
-// collects the device error bits.
+// the seed J * density (linear density: J).  In the FP32 path the seed is
+// formed in FP64 (Jacobian of Eq. (map4) from the FP64 vertices, times the
+// FP64 density) and rounded once to FP32; the densities the linear chain
+// reads are rounded to FP32.  An inactive lane, a bad vertex index or a
+// non-finite input gives an all-zero frame and pL = -1; errbits collects the
+// device error bits.
 template <typename T, int NL>
 struct Frame {
     T LX[NL], LY[NL], LZ[NL];  // stencil vertex of each level: X = x/2, Y = y/2, z
@@ -688,6 +714,8 @@ __device__ __forceinline__ void load_frame(const double* __restrict__ vx, const 
     T vxl[NV], vyl[NV], vzl[NV];
     T edge[NV - 1][3];  // x_k - x1 in the scaled frame, k = 2..NV
     T s1 = T(0), s2 = T(0), s3 = T(0);
+    double xd[NV][3];   // FP32 path: the FP64 vertices, for the FP64 seed
+    double dens0 = 0.0;
     bool bad = !active;
     {
         int64_t vid[NV];
@@ -711,12 +739,12 @@ __device__ __forceinline__ void load_frame(const double* __restrict__ vx, const 
             }
         }
         if constexpr (FP32) {
-            bool nf = false;
-            float lo;
+            bool nf = !(finite_bits(dens[0]) && finite_bits(dens[1]) && finite_bits(dens[2]));
+            s1 = __double2float_rn(dens[0]);
+            s2 = __double2float_rn(dens[1]);
+            s3 = __double2float_rn(dens[2]);
+            dens0 = dens[0];
             float sh[NV][3], sl[NV][3];
-            split_f64(dens[0], s1, lo, nf);
-            split_f64(dens[1], s2, lo, nf);
-            split_f64(dens[2], s3, lo, nf);
             float chx, clx, chy, cly, chz, clz;
             split_f64(cx, chx, clx, nf);
             split_f64(cy, chy, cly, nf);
@@ -725,9 +753,12 @@ __device__ __forceinline__ void load_frame(const double* __restrict__ vx, const 
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
                 float hx, lx, hy, ly, hz, lz;
-                split_f64(active ? __ldg(vx + vid[k]) : 0.0, hx, lx, nf);
-                split_f64(active ? __ldg(vy + vid[k]) : 0.0, hy, ly, nf);
-                split_f64(active ? __ldg(vz + vid[k]) : 0.0, hz, lz, nf);
+                xd[k][0] = active ? __ldg(vx + vid[k]) : 0.0;
+                xd[k][1] = active ? __ldg(vy + vid[k]) : 0.0;
+                xd[k][2] = active ? __ldg(vz + vid[k]) : 0.0;
+                split_f64(xd[k][0], hx, lx, nf);
+                split_f64(xd[k][1], hy, ly, nf);
+                split_f64(xd[k][2], hz, lz, nf);
                 vxl[k] = ((hx - chx) + (lx - clx)) * inv;
                 vyl[k] = ((hy - chy) + (ly - cly)) * inv;
                 vzl[k] = ((hz - chz) + (lz - clz)) * inv;
@@ -809,8 +840,35 @@ __device__ __forceinline__ void load_frame(const double* __restrict__ vx, const 
             }
         }
     }
-    T seed = LIN ? J : J * s1;
-    if (pL < 0) seed = T(0);
+    T seed;
+    if constexpr (FP32) {
+        // Jacobian (Eq. (map4)) and seed in FP64, once per element; the frame
+        // scale 2^-sexp enters as an exact power of two per dimension
+        double ed[NV - 1][3];
+#pragma unroll
+        for (int k = 1; k < NV; ++k)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) ed[k - 1][d] = xd[k][d] - xd[0][d];
+        double J64;
+        if constexpr (KIND == KIND_SEG) {
+            J64 = sqrt(ed[0][0] * ed[0][0] + ed[0][1] * ed[0][1] + ed[0][2] * ed[0][2]);
+        } else {
+            const int kv = NV >= 3 ? 1 : 0;
+            const double qx = ed[0][1] * ed[kv][2] - ed[0][2] * ed[kv][1];
+            const double qy = ed[0][2] * ed[kv][0] - ed[0][0] * ed[kv][2];
+            const double qz = ed[0][0] * ed[kv][1] - ed[0][1] * ed[kv][0];
+            if constexpr (KIND == KIND_TRI)
+                J64 = sqrt(qx * qx + qy * qy + qz * qz);
+            else
+                J64 = fabs(qx * ed[NV - 2][0] + qy * ed[NV - 2][1] + qz * ed[NV - 2][2]);
+        }
+        J64 *= pow2d(-(KIND + 1) * sexp);
+        const double seed64 = LIN ? J64 : J64 * dens0;
+        seed = (bad || pL < 0) ? 0.f : __double2float_rn(seed64);
+    } else {
+        seed = LIN ? J : J * s1;
+        if (pL < 0) seed = T(0);
+    }
 
     // stencil coefficients of each level: X = x/2, Y = y/2, z
 #pragma unroll
@@ -1080,14 +1138,14 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
 }
 
 // Shared memory per warp: stage tile [2 layers][CHUNK][LD] of T, open-run sums
-// [2 layers][np_max] of T, row leaves [32], row infos [32].
+// [2 layers][np_max] (LeafSum, 8 bytes), row leaves [32], row infos [32].
 // (rounded up to 128 bytes so every warp's tile keeps the 16-byte alignment of
 // the 128-bit column loads)
 template <typename T>
 __host__ __device__ constexpr size_t warp_smem_bytes(int np_max)
 {
-    return (sizeof(T) * (size_t)(2 * KCfg<T>::CHUNK * KCfg<T>::LD + 2 * np_max) + sizeof(long long) * 32 +
-            sizeof(int) * 32 + 127) / 128 * 128;
+    return (sizeof(T) * (size_t)(2 * KCfg<T>::CHUNK * KCfg<T>::LD) + sizeof(LeafSum<T>) * (size_t)(2 * np_max) +
+            sizeof(long long) * 32 + sizeof(int) * 32 + 127) / 128 * 128;
 }
 
 template <typename T, int P>
@@ -1114,7 +1172,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
 
     unsigned char* wsm = smem_raw + (size_t)wib * warp_smem_bytes<T>(a.np_max);
     T* tile = reinterpret_cast<T*>(wsm);
-    T* accb = tile + 2 * CH * LD;
+    LeafSum<T>* accb = reinterpret_cast<LeafSum<T>*>(tile + 2 * CH * LD);  // 2 CH LD sizeof(T) % 8 == 0
     long long* rowleaf = reinterpret_cast<long long*>(accb + 2 * a.np_max);
     int* rowinfo = reinterpret_cast<int*>(rowleaf + 32);
 
@@ -1142,7 +1200,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
         L_last = leaf_search(a.leaf_off, rc.L_first, a.n_leaves - 1, rc.e_hi - 1);
     }
 
-    for (int k = lane; k < 2 * np; k += 32) accb[k] = T(0);
+    for (int k = lane; k < 2 * np; k += 32) accb[k].zero();
 
     // zero the coefficients of empty leaves [La, Lb) (overwrite mode)
     auto zero_leaves = [&](int64_t La, int64_t Lb) {
@@ -1280,10 +1338,9 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
 
 // Combine the slot partials of leaves that span several warp ranges.  One warp
 // per range boundary w (1 <= w < n_ranges): the leaf L containing element w*T,
-// handled here iff w is the last range L touches.  Partials are summed in range
-// order (compensated in FP32), then scaled like a complete run.
-template <typename T>
-__global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d1)
+// handled here iff w is the last range L touches.  The FP64 partials are summed
+// in range order (compensated), then scaled like a complete run.
+static __global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d1)
 {
     const int lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1;
@@ -1303,16 +1360,16 @@ __global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d1)
         if (pl < 0 || pl > a.p_max) pl = -1;
     }
     const int np = a.np_max;
-    const T* slots = reinterpret_cast<const T*>(a.slots);
+    const double* slots = a.slots;
     for (int ly = 0; ly < 2; ++ly) {
         if (a.coef[ly] == nullptr) continue;
         for (int c = lane; c < np; c += 32) {
-            T sum = slots[((wf * 2 + slot_first) * 2 + ly) * (int64_t)np + c];
-            T comp = T(0);
+            double sum = slots[((wf * 2 + slot_first) * 2 + ly) * (int64_t)np + c];
+            double comp = 0.0;
             for (int64_t ww = wf + 1; ww <= w; ++ww) {
-                const T x = slots[((ww * 2 + 0) * 2 + ly) * (int64_t)np + c];
+                const double x = slots[((ww * 2 + 0) * 2 + ly) * (int64_t)np + c];
                 // Kahan-Babuska (Neumaier) step
-                const T t = sum + x;
+                const double t = sum + x;
                 if (fabs(sum) >= fabs(x))
                     comp += (sum - t) + x;
                 else
@@ -1338,23 +1395,43 @@ __global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d1)
 namespace q2x {
 
 // Launch helpers (explicitly instantiated in q2x_inst_*.cu).
+//
+// The dynamic shared-memory limit of an instantiation is raised once per
+// device, to what its largest degree (P) needs, and not on every launch: a
+// plan's p_max <= P needs no more (warp_smem_bytes grows with the column count).
+constexpr int kMaxDevices = 64;
+
+template <typename T, int P, int KIND, int DENS, int OUTS>
+cudaError_t elem_smem_attribute()
+{
+    static int done[kMaxDevices] = {};  // 0 not yet, 1 set (benign race: the set is idempotent)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDevices && done[dev]) return cudaSuccess;
+    const size_t smem_max = WARPS_PER_CTA * warp_smem_bytes<T>((P + 1) * (P + 1));
+    e = cudaFuncSetAttribute(q2x_elem_kernel<T, P, KIND, DENS, OUTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_max);
+    if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) done[dev] = 1;
+    return e;
+}
+
 template <typename T, int P, int KIND, int DENS, int OUTS>
 cudaError_t launch_elem(const ElemArgs& a, int grid, size_t smem, cudaStream_t st)
 {
-    auto k = q2x_elem_kernel<T, P, KIND, DENS, OUTS>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = elem_smem_attribute<T, P, KIND, DENS, OUTS>();
     if (e != cudaSuccess) return e;
-    k<<<grid, WARPS_PER_CTA * 32, smem, st>>>(a);
+    q2x_elem_kernel<T, P, KIND, DENS, OUTS><<<grid, WARPS_PER_CTA * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T, int P, int KIND, int DENS, int OUTS>
 cudaError_t occupancy_elem(int* blocks_per_sm, size_t smem)
 {
-    auto k = q2x_elem_kernel<T, P, KIND, DENS, OUTS>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = elem_smem_attribute<T, P, KIND, DENS, OUTS>();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, WARPS_PER_CTA * 32, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, q2x_elem_kernel<T, P, KIND, DENS, OUTS>,
+                                                         WARPS_PER_CTA * 32, smem);
 }
 
 }  // namespace q2x

@@ -19,7 +19,11 @@
 // Every call on a device shares the one array, which keeps the previous call's
 // contents; the kernels write every scratch entry they read within a call, so
 // nothing needs clearing.  Calls that overlap on the GPU (different streams,
-// or host threads) race on the array and on the device error word.
+// or host threads) race on the array and on the device error word.  Nothing
+// here reads that word back: device-side input checks are not reported, and
+// leaf_off is not checked on the device (the kernels still keep every access
+// in bounds; a non-monotone or out-of-range leaf_off gives undefined
+// coefficients).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -58,18 +62,6 @@ const LaunchFn kTri[2][2][3][5] = {
     {Q2X_NA_DENS(double, q2x::DENS_CONST) Q2X_NA_DENS(double, q2x::DENS_LINEAR)},
     {Q2X_NA_DENS(float, q2x::DENS_CONST) Q2X_NA_DENS(float, q2x::DENS_LINEAR)},
 };
-
-__global__ void noalloc_check_leaf_off(const int64_t* off, int64_t n_leaves, int64_t n_elem, unsigned* err)
-{
-    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (L > n_leaves) return;
-    const int64_t o = off[L];
-    bool bad = (o < 0 || o > n_elem);
-    if (L == 0 && o != 0) bad = true;
-    if (L == n_leaves && o != n_elem) bad = true;
-    if (L < n_leaves && off[L + 1] < o) bad = true;
-    if (bad) atomicOr(err, Q2X_DEVERR_LEAF_OFF);
-}
 
 // Device addresses of the scratch array and error word on the current device
 // (looked up once per device).
@@ -121,22 +113,33 @@ extern "C" q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precis
     if (n_elem > 0 && (!vxyz || !idx || !sigma || n_vert <= 0 || n_leaves <= 0)) return Q2X_ERR_ARG;
 
     const int prec = (precision == Q2X_FP32_MIXED) ? 1 : 0;
-    const size_t elt = prec ? sizeof(float) : sizeof(double);
+    const int64_t elt = (int64_t)sizeof(double);  // FP64 partial sums in both precisions
     const int np = (p_max + 1) * (p_max + 1);
     const int64_t T = Q2X_NOALLOC_RANGE;
+    // size limit by division (no product that could wrap): each range needs
+    // 4 np elt bytes of scratch
+    const int64_t max_ranges = (int64_t)Q2X_NOALLOC_SCRATCH_BYTES / (4 * (int64_t)np * elt);
+    if (n_elem > max_ranges * T) return Q2X_ERR_RANGE;
     const int64_t n_ranges = (n_elem + T - 1) / T;
-    if ((size_t)n_ranges * 4 * np * elt > (size_t)Q2X_NOALLOC_SCRATCH_BYTES) return Q2X_ERR_RANGE;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return Q2X_ERR_CUDA;
     }
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (stream) {  // the scratch address is the current device's: the stream must be on it
+        int sdev = -1;
+        if (cudaStreamGetDevice(stream, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return Q2X_ERR_ARG;
+        }
+        if (sdev != dev) return Q2X_ERR_ARG;
+    }
     void* scratch = nullptr;
     unsigned* err = nullptr;
     q2x_status st = noalloc_setup(dev, &scratch, &err);
     if (st != Q2X_OK) return st;
-    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
     if (n_elem == 0) {
         if (!accumulate)
@@ -172,10 +175,9 @@ extern "C" q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precis
     a.norm = (int)norm;
     a.T = T;
     a.n_ranges = n_ranges;
-    a.slots = scratch;
+    a.slots = static_cast<double*>(scratch);
     a.err = err;
 
-    noalloc_check_leaf_off<<<(unsigned)((n_leaves + 1 + 255) / 256), 256, 0, stream>>>(leaf_off, n_leaves, n_elem, err);
     const size_t smem = q2x::WARPS_PER_CTA *
                         (prec ? q2x::warp_smem_bytes<float>(np) : q2x::warp_smem_bytes<double>(np));
     const int grid = (int)((n_ranges + q2x::WARPS_PER_CTA - 1) / q2x::WARPS_PER_CTA);
@@ -184,10 +186,7 @@ extern "C" q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precis
     if (n_ranges > 1) {
         const int d_out = (density == Q2X_DENSITY_LINEAR) ? 3 : 2;
         const int fgrid = (int)((n_ranges - 1 + 3) / 4);
-        if (prec)
-            q2x::q2x_fixup_kernel<float><<<fgrid, 128, 0, stream>>>(a, 2, d_out, d_out - 1);
-        else
-            q2x::q2x_fixup_kernel<double><<<fgrid, 128, 0, stream>>>(a, 2, d_out, d_out - 1);
+        q2x::q2x_fixup_kernel<<<fgrid, 128, 0, stream>>>(a, 2, d_out, d_out - 1);
         if (cudaGetLastError() != cudaSuccess) return Q2X_ERR_CUDA;
     }
     return Q2X_OK;

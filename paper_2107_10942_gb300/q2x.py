@@ -477,6 +477,22 @@ def local_expansion_weights(L_re, L_im, p):
     return w
 
 
+PEAK_KINDS = {"dfma": 0, "ffma": 1, "ffma2": 2}
+
+
+def alu_peak_probe(kind: str, iters: int, sink, stream=None) -> float:
+    """Launch the library's FMA-chain probe (q2x_alu_peak_probe) on `stream`
+    (default: the current stream); returns the flops the launch performs.
+    `sink` is a one-element float64 CUDA tensor."""
+    _need(sink, torch.float64, "sink")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    flops = ctypes.c_double(0.0)
+    check(lib().q2x_alu_peak_probe(PEAK_KINDS[kind], int(iters), _ptr(sink), ctypes.c_void_p(stream.cuda_stream),
+                                   ctypes.byref(flops)))
+    return float(flops.value)
+
+
 def problem_to_device(prob: dict, device="cuda") -> dict:
     """Copy a workloads-style problem dict (numpy arrays) to device tensors."""
     out = {}

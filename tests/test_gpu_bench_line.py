@@ -30,10 +30,20 @@ def test_headline_json_line():
     r = d["roofline"]
     for key in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
         assert key in r, key
-    assert 0.0 < r["frac"] < 1.5 and r["executed"]["frac"] > 0
+    assert 0.0 < r["frac"] < 1.5
+    assert r["executed"] is None or r["executed"]["frac"] > 0
+    assert r["peak_source"].startswith("measured")
+    pk = d["alu_peaks_measured"]
+    assert pk["dfma"]["tflops"] > 0.5 and max(pk["ffma"]["tflops"], pk["ffma2"]["tflops"]) > 30
+    assert d["fp32_mixed"]["roofline"]["frac"] > 0
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     c = d["cpu_baseline"]
     assert c["kind"] == "oracle" and c["cores"] >= 1 and c["value"] > 0 and c["single_core"]["cores"] == 1
     assert d["gpu_launches"] > 0 and "workload" in d["config"]
     assert d["errors_vs_oracle"]["fp64"]["single"] <= 1e-12 and d["errors_vs_oracle"]["fp32"]["single"] <= 1e-5
+    # the clock record covers both precision arms
+    wins = d["clocks"]["windows"]
+    assert any(k.startswith("fp64") for k in wins) and any(k.startswith("fp32") for k in wins)
+    eq = d["speedup_at_equal_accuracy"]
+    assert eq["speedup"] > 1 and len(eq["by_distance"]) == 3
