@@ -381,8 +381,8 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     const int bin = bin_index(plan->p_max);
     if (bin < 0) return fail(plan, Q2X_ERR_RANGE, "p_max %d above %d", plan->p_max, Q2X_P_MAX);
     const KernelEntry& ke = kTable[prec][combo][bin];
-    const size_t smem = q2x::WARPS_PER_CTA *
-                        (prec ? q2x::warp_smem_bytes<float>(np) : q2x::warp_smem_bytes<double>(np));
+    const int wpc = prec ? q2x::elem_warps_per_cta<float>() : q2x::elem_warps_per_cta<double>();
+    const size_t smem = wpc * (prec ? q2x::warp_smem_bytes<float>(np) : q2x::warp_smem_bytes<double>(np));
 
     int& occ = plan->occ_cache[prec][combo][bin];
     if (occ == 0) {
@@ -390,7 +390,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
         if (e != cudaSuccess) return cuda_fail(plan, e, "occupancy query");
         if (occ <= 0) return fail(plan, Q2X_ERR_CUDA, "kernel does not fit on the device (smem %zu)", smem);
     }
-    const int64_t resident_warps = (int64_t)occ * q2x::WARPS_PER_CTA * plan->num_sms;
+    const int64_t resident_warps = (int64_t)occ * wpc * plan->num_sms;
     // one range per resident warp (ranges need not be multiples of 32: rounds
     // are formed per leaf inside the kernel), at least one full round each
     int64_t T = (n_elem + resident_warps - 1) / resident_warps;
@@ -448,7 +448,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     a.err = plan->d_err;
     a.raw = raw;
 
-    const int grid = (int)((n_ranges + q2x::WARPS_PER_CTA - 1) / q2x::WARPS_PER_CTA);
+    const int grid = (int)((n_ranges + wpc - 1) / wpc);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (plan->timing) {
         st = take_event(plan, &ev0);

@@ -68,7 +68,19 @@ namespace q2x {
 enum : int { KIND_SEG = 0, KIND_TRI = 1, KIND_TET = 2 };
 enum : int { DENS_CONST = 0, DENS_LINEAR = 1 };
 
-constexpr int WARPS_PER_CTA = 4;
+constexpr int WARPS_PER_CTA = 4;  // CTAs of the FP64 element kernel and of the Galerkin kernel
+
+// Warps per CTA of the element kernel.  Warps never cooperate (each owns its
+// range and its shared-memory region), so FP32 CTAs are single warps: the
+// number of resident warps is then set by the registers alone, which are
+// allotted per SM sub-partition (16 K each: 4 warps at <= 128 registers, 3 at
+// <= 168, 2 at <= 256).  The FP64 kernel keeps CTAs of four warps (measured
+// 2 % faster than single warps at the same occupancy).
+template <typename T>
+__host__ __device__ constexpr int elem_warps_per_cta()
+{
+    return sizeof(T) == 4 ? 1 : WARPS_PER_CTA;
+}
 
 // Stage tile geometry per precision: CHUNK columns per layer, LD = padded
 // row stride (36 floats keeps 16-byte aligned columns for 128-bit loads and
@@ -899,7 +911,7 @@ __device__ __forceinline__ void load_frame(const double* __restrict__ vx, const 
 // stage each degree's single- and double-layer values of this lane's element
 // in column order of the stage tile (layer 1 at tile + CHUNK*LD), and call
 // reduce(c0, ncols) whenever a chunk of columns [c0, c0 + ncols) is complete.
-template <typename T, int P, int KIND, int DENS, int OUTS, typename Reduce>
+template <typename T, int P, int KIND, int DENS, int OUTS, bool WIDE = false, typename Reduce>
 __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>& F, int pw, T* tile,
                                           int lane, Reduce&& reduce)
 {
@@ -911,6 +923,9 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
     constexpr bool LIN = (KIND == KIND_TRI && DENS == DENS_LINEAR);
     constexpr bool want0 = (OUTS & 1) != 0;
     constexpr bool want1 = (KIND == KIND_TRI) && (OUTS & 2) != 0;
+    // columns staged per chunk: a single-layer pass may use both halves of a
+    // two-layer tile (WIDE), which halves the reductions per round
+    constexpr int CAP = (WIDE && !want1) ? 2 * CH : CH;
     const T s1 = F.s1, s2 = F.s2, s3 = F.s3, seed = F.seed;
     const T XN = F.XN, YN = F.YN, ZN = F.ZN;
     const T* LX = F.LX;
@@ -1011,7 +1026,7 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                     }
                 }
             }
-            if (n == pw || (n + 2) * (n + 2) - nb * nb > CH) {
+            if (n == pw || (n + 2) * (n + 2) - nb * nb > CAP) {
                 __syncwarp();
                 reduce(nb * nb, (n + 1) * (n + 1) - nb * nb);
                 __syncwarp();
@@ -1127,7 +1142,7 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                 else if (m == n)
                     body(m_c, FF{}, FF{});
             });
-            if (n == pw || (n + 2) * (n + 2) - nb * nb > CH) {
+            if (n == pw || (n + 2) * (n + 2) - nb * nb > CAP) {
                 __syncwarp();
                 reduce(nb * nb, (n + 1) * (n + 1) - nb * nb);
                 __syncwarp();
@@ -1148,16 +1163,28 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int np_max)
             sizeof(long long) * 32 + sizeof(int) * 32 + 127) / 128 * 128;
 }
 
-template <typename T, int P>
+// Resident CTAs per SM the element kernel is compiled for, which caps its
+// registers: FP32 chains whose rows leave room run 4 warps per sub-partition
+// (segments up to P = 16, constant-density single-layer triangles up to
+// P = 8) or 3 (those triangles up to P = 16), without spills; the rest, and
+// FP64, 2 warps per sub-partition (no cap below 255 registers).
+template <typename T, int P, int KIND, int DENS, int OUTS>
 __host__ __device__ constexpr int min_ctas()
 {
-    return 2;  // no register spills for the row arrays at P <= 12 (measured best on GB300)
+    if constexpr (sizeof(T) == 4) {
+        if (KIND == KIND_SEG && P <= 16) return 16;
+        if (KIND == KIND_TRI && DENS == DENS_CONST && OUTS == 1 && P <= 8) return 16;
+        if (KIND == KIND_TRI && DENS == DENS_CONST && OUTS == 1 && P <= 16) return 12;
+        return 8;
+    } else {
+        return 2;
+    }
 }
 
 // OUTS: bit 0 = single layer, bit 1 = double layer (triangles); a compile-time
 // choice so each kernel holds exactly one copy of the degree loop.
 template <typename T, int P, int KIND, int DENS, int OUTS>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
+__global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, KIND, DENS, OUTS>()))
     q2x_elem_kernel(const ElemArgs a)
 {
     using C = Chain<KIND, DENS>;
@@ -1167,7 +1194,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int64_t w = (int64_t)blockIdx.x * WARPS_PER_CTA + wib;
+    const int64_t w = (int64_t)blockIdx.x * elem_warps_per_cta<T>() + wib;
     if (w >= a.n_ranges) return;
 
     unsigned char* wsm = smem_raw + (size_t)wib * warp_smem_bytes<T>(a.np_max);
@@ -1315,7 +1342,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (min_ctas<T, P>()))
         load_frame<T, KIND, DENS>(a.vx, a.vy, a.vz, a.idx, a.sigma, a.n_elem, a.n_vert, e, active, cx, cy, cz, sexp,
                                   errbits, pL, F);
         if (errbits) atomicOr(a.err, errbits);
-        run_chain<T, P, KIND, DENS, OUTS>(F, pw, tile, lane, [&](int c0, int ncols) {
+        run_chain<T, P, KIND, DENS, OUTS, true>(F, pw, tile, lane, [&](int c0, int ncols) {
             reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, gstart, n_taken, c0, ncols,
                             want0, want1, per_elem);
         });
@@ -1409,7 +1436,7 @@ cudaError_t elem_smem_attribute()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < kMaxDevices && done[dev]) return cudaSuccess;
-    const size_t smem_max = WARPS_PER_CTA * warp_smem_bytes<T>((P + 1) * (P + 1));
+    const size_t smem_max = elem_warps_per_cta<T>() * warp_smem_bytes<T>((P + 1) * (P + 1));
     e = cudaFuncSetAttribute(q2x_elem_kernel<T, P, KIND, DENS, OUTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_max);
     if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) done[dev] = 1;
@@ -1421,7 +1448,7 @@ cudaError_t launch_elem(const ElemArgs& a, int grid, size_t smem, cudaStream_t s
 {
     cudaError_t e = elem_smem_attribute<T, P, KIND, DENS, OUTS>();
     if (e != cudaSuccess) return e;
-    q2x_elem_kernel<T, P, KIND, DENS, OUTS><<<grid, WARPS_PER_CTA * 32, smem, st>>>(a);
+    q2x_elem_kernel<T, P, KIND, DENS, OUTS><<<grid, elem_warps_per_cta<T>() * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1431,7 +1458,7 @@ cudaError_t occupancy_elem(int* blocks_per_sm, size_t smem)
     cudaError_t e = elem_smem_attribute<T, P, KIND, DENS, OUTS>();
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, q2x_elem_kernel<T, P, KIND, DENS, OUTS>,
-                                                         WARPS_PER_CTA * 32, smem);
+                                                         elem_warps_per_cta<T>() * 32, smem);
 }
 
 }  // namespace q2x

@@ -178,9 +178,9 @@ extern "C" q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precis
     a.slots = static_cast<double*>(scratch);
     a.err = err;
 
-    const size_t smem = q2x::WARPS_PER_CTA *
-                        (prec ? q2x::warp_smem_bytes<float>(np) : q2x::warp_smem_bytes<double>(np));
-    const int grid = (int)((n_ranges + q2x::WARPS_PER_CTA - 1) / q2x::WARPS_PER_CTA);
+    const int wpc = prec ? q2x::elem_warps_per_cta<float>() : q2x::elem_warps_per_cta<double>();
+    const size_t smem = wpc * (prec ? q2x::warp_smem_bytes<float>(np) : q2x::warp_smem_bytes<double>(np));
+    const int grid = (int)((n_ranges + wpc - 1) / wpc);
     const int outs = (coef_single ? 1 : 0) | (coef_double ? 2 : 0);
     if (kTri[prec][density][outs - 1][bin](a, grid, smem, stream) != cudaSuccess) return Q2X_ERR_CUDA;
     if (n_ranges > 1) {
