@@ -59,13 +59,14 @@ DEFAULT_WORKLOAD = "sphere-L9-const"
 # Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) and
 # executed flops of the element kernels, from one ncu capture of the current
 # kernel on each workload (None: not captured since the kernel last changed).
-# Executed flops: FP64 2 x DFMA + DADD + DMUL, FP32 2 x FFMA + FADD + FMUL
-# thread instructions.
+# Executed flops: FP64 2 x DFMA + DADD + DMUL thread instructions; FP32
+# 4 x FFMA2 + 2 x FFMA + 2 x FADD2 + FADD + FMUL (per-opcode thread counts:
+# the packed instructions are not in the FFMA/FADD class counters).
 KERNEL_COUNTERS = {
-    ("sphere-L9-const", "fp64"): dict(traffic=None, executed_flops=None),
-    ("sphere-L9-const", "fp32"): dict(traffic=None, executed_flops=None),
-    ("sphere-L7-linear", "fp64"): dict(traffic=None, executed_flops=None),
-    ("sphere-L7-linear", "fp32"): dict(traffic=None, executed_flops=None),
+    ("sphere-L9-const", "fp64"): dict(traffic=236734208 + 130404096, executed_flops=35717877081),
+    ("sphere-L9-const", "fp32"): dict(traffic=221895680 + 112655360, executed_flops=41174200000),
+    ("sphere-L7-linear", "fp64"): dict(traffic=9746944 + 40769280, executed_flops=2859759419),
+    ("sphere-L7-linear", "fp32"): dict(traffic=9387776 + 256, executed_flops=3403620000),
 }
 COUNTER_SOURCE = "ncu --set full capture of one launch of this kernel on this workload"
 

@@ -424,12 +424,12 @@ q2x_status q2x_leaf_reduce(q2x_plan_t plan, int64_t n_elem, int p, const double*
  * (component j's block at coef3 + j * n_leaves * (p_max+1)^2), otherwise the
  * arguments of q2x_segments (leaf_off required).  The moments are geometric
  * and each component multiplies them, so the recursion runs once per
- * element: a per-element pass stores each element's unfinished moments about
- * its leaf's centre (chunks of at most 4 GiB of rows, stream-ordered
- * allocation on the plan's stream), then one weighted segmented sum per
- * (leaf, column) forms the three components and finishes them.  Same
- * results as three q2x_segments calls with the components as densities, up
- * to rounding; deterministic. */
+ * element, with unit density: each round's moments are staged once and summed
+ * per leaf three times, weighted by the components (one pass of the element
+ * kernel; no temporary beyond the plan workspace).  Same results as three
+ * q2x_segments calls with the components as densities, up to rounding;
+ * deterministic.  A non-finite component sets Q2X_DEVERR_NONFINITE and its
+ * segment contributes zero. */
 q2x_status q2x_segments_vector(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, const double* vxyz,
                                const int32_t* idx, const double* current, int64_t n_leaves,
                                const int64_t* leaf_off, const double* leaf_c, const double* leaf_rho,

@@ -22,7 +22,8 @@
     Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_LINEAR, 1)                               \
     Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_LINEAR, 2)                               \
     Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TRI, q2x::DENS_LINEAR, 3)                               \
-    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TET, q2x::DENS_CONST, 1)
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_TET, q2x::DENS_CONST, 1)                                \
+    Q2X_FOR_BINS(Q2X_DECLARE, T, q2x::KIND_SEG, q2x::DENS_CONST, 4)
 Q2X_DECLARE_ALL(float)
 Q2X_DECLARE_ALL(double)
 
@@ -35,7 +36,7 @@ struct KernelEntry {
 
 constexpr int kNumBins = 5;
 constexpr int kBins[kNumBins] = {4, 8, 12, 16, 20};
-constexpr int kNumCombos = 8;
+constexpr int kNumCombos = 9;
 
 #define Q2X_ENTRY(T, P, KIND, DENS, OUTS) \
     {&q2x::launch_elem<T, P, KIND, DENS, OUTS>, &q2x::occupancy_elem<T, P, KIND, DENS, OUTS>},
@@ -44,13 +45,16 @@ constexpr int kNumCombos = 8;
     {Q2X_ROW(T, q2x::KIND_SEG, q2x::DENS_CONST, 1) Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_CONST, 1)              \
          Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_CONST, 2) Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_CONST, 3)          \
              Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_LINEAR, 1) Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_LINEAR, 2)   \
-                 Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_LINEAR, 3) Q2X_ROW(T, q2x::KIND_TET, q2x::DENS_CONST, 1)}
+                 Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_LINEAR, 3) Q2X_ROW(T, q2x::KIND_TET, q2x::DENS_CONST, 1)    \
+                     Q2X_ROW(T, q2x::KIND_SEG, q2x::DENS_CONST, 4)}
 // [precision: 0 FP64, 1 FP32][combo][bin]; combos: 0 segments, 1-3 triangles
-// constant density (single, double, both), 4-6 linear density, 7 tetrahedra
+// constant density (single, double, both), 4-6 linear density, 7 tetrahedra,
+// 8 segments carrying a vector density
 const KernelEntry kTable[2][kNumCombos][kNumBins] = {Q2X_ROWS(double), Q2X_ROWS(float)};
 
-int combo_index(int kind, int dens, bool single, bool dbl)
+int combo_index(int kind, int dens, bool single, bool dbl, bool vec = false)
 {
+    if (vec) return 8;
     if (kind == q2x::KIND_SEG) return 0;
     if (kind == q2x::KIND_TET) return 7;
     const int outs = (single ? 1 : 0) | (dbl ? 2 : 0);
@@ -252,106 +256,30 @@ __global__ void leaf_reduce_weighted_kernel(const double* __restrict__ elem, int
     }
 }
 
-// Per-element copies of the leaf data for the per-element pass over the
-// elements [e0, e0 + m) of a vector density: each element's leaf centre,
-// scale and degree, its vertex indices, and a unit density.
-__global__ void vector_gather_kernel(const int64_t* __restrict__ off, int64_t n_leaves,
-                                     const double* __restrict__ leaf_c, const double* __restrict__ rho,
-                                     const int32_t* __restrict__ leaf_p, const int32_t* __restrict__ idx,
-                                     int64_t n_elem, int64_t e0, int64_t m, double* ec, double* er, int32_t* ep,
-                                     int32_t* idxc, double* ones)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const int64_t e = e0 + i;
-    const int64_t L = q2x::leaf_search(off, 0, n_leaves - 1, e);
-    ec[i] = __ldg(leaf_c + L);
-    ec[m + i] = __ldg(leaf_c + n_leaves + L);
-    ec[2 * m + i] = __ldg(leaf_c + 2 * n_leaves + L);
-    if (er) er[i] = __ldg(rho + L);
-    if (ep) ep[i] = __ldg(leaf_p + L);
-    idxc[i] = __ldg(idx + e);
-    idxc[m + i] = __ldg(idx + n_elem + e);
-    ones[i] = 1.0;
-}
-
-// The three components of a vector density from the unfinished per-element
-// rows of the elements [e0, e1): per (leaf, column), the weighted sums
-// sum_e cur[j][e] rows[e] in element order, finished once per leaf (the
-// finish is linear: 1/(n+d)!, the packing sign, 1/4pi, the leaf's scale).
-__global__ void vector_reduce_kernel(const double* __restrict__ rows, int np, int64_t e0, int64_t e1,
-                                     int64_t n_elem, const double* __restrict__ cur, int64_t n_leaves,
-                                     const int64_t* __restrict__ off, const double* __restrict__ rho,
-                                     const int32_t* __restrict__ leaf_p, int p_max, int norm, int d, int shift_n0,
-                                     double* coef, int accumulate)
-{
-    constexpr int U = 8;
-    // one warp per (leaf, 32 columns): the leaf's weights are read once per warp
-    const int lane = threadIdx.x & 31;
-    const int groups = (np + 31) >> 5;
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t L = gw / groups;
-    if (L >= n_leaves) return;
-    const int c = (int)(gw - L * groups) * 32 + lane;
-    if (c >= np) return;
-    const int64_t lo = min(max(max(off[L], (int64_t)0), e0), e1);
-    const int64_t hi = min(max(min(off[L + 1], n_elem), lo), e1);
-    if (lo == hi && accumulate) return;  // nothing of this leaf in the chunk
-    const double* col = rows + c;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    int64_t e = lo;
-    for (; e + U <= hi; e += U) {
-        double v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = __ldg(col + (e + u - e0) * np);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            a0 = fma(__ldg(cur + e + u), v[u], a0);
-            a1 = fma(__ldg(cur + n_elem + e + u), v[u], a1);
-            a2 = fma(__ldg(cur + 2 * n_elem + e + u), v[u], a2);
-        }
-    }
-    for (; e < hi; ++e) {
-        const double v = __ldg(col + (e - e0) * np);
-        a0 = fma(__ldg(cur + e), v, a0);
-        a1 = fma(__ldg(cur + n_elem + e), v, a1);
-        a2 = fma(__ldg(cur + 2 * n_elem + e), v, a2);
-    }
-    const int desc = q2x::col_desc(c);
-    int pl = p_max;
-    if (leaf_p) {
-        pl = __ldg(leaf_p + L);
-        if (pl < 0 || pl > p_max) pl = -1;
-    }
-    const int s = rho ? q2x::scale_exponent(__ldg(rho + L)) : 0;
-    const bool keep = (desc & 31) <= pl;
-    const double acc[3] = {a0, a1, a2};
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const double v = keep ? q2x::finish_desc(acc[j], norm, desc, d, shift_n0, s) : 0.0;
-        double* dst = coef + (j * n_leaves + L) * (int64_t)np + c;
-        *dst = accumulate ? *dst + v : v;
-    }
-}
-
 // --------------------------------------------------------------- dispatch
 
 q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int64_t n_vert,
                         const double* vxyz, const int32_t* idx, const double* sigma,
                         int64_t n_leaves, const int64_t* leaf_off, const double* leaf_c,
                         const double* leaf_rho, const int32_t* leaf_p, double* coef0,
-                        double* coef1, int accumulate, int raw = 0)
+                        double* coef1, int accumulate, const double* wvec = nullptr, double* coef2 = nullptr)
 {
+    // wvec: a vector density (segments): the three components weight one
+    // unit-density pass, into coef0, coef1, coef2
+    const bool vec = wvec != nullptr;
     if (!plan) return fail(nullptr, Q2X_ERR_ARG, "plan is NULL");
     if (n_elem < 0 || n_vert < 0 || n_leaves < 0)
         return fail(plan, Q2X_ERR_ARG, "negative size (n_elem=%lld n_vert=%lld n_leaves=%lld)",
                     (long long)n_elem, (long long)n_vert, (long long)n_leaves);
-    if (!coef0 && !coef1) return fail(plan, Q2X_ERR_ARG, "no output requested");
+    if (!coef0 && !coef1 && !coef2) return fail(plan, Q2X_ERR_ARG, "no output requested");
+    if (vec && (kind != q2x::KIND_SEG || !leaf_off))
+        return fail(plan, Q2X_ERR_ARG, "a vector density needs segments in leaf mode");
     if (accumulate != 0 && accumulate != 1) return fail(plan, Q2X_ERR_ARG, "accumulate must be 0 or 1");
     if (!leaf_off && n_leaves != n_elem)
         return fail(plan, Q2X_ERR_ARG, "per-element mode (leaf_off NULL) needs n_leaves == n_elem");
     if (n_elem > 0) {
-        if (!vxyz || !idx || !sigma) return fail(plan, Q2X_ERR_ARG, "vxyz, idx and sigma must be non-NULL");
+        if (!vxyz || !idx || (!sigma && !vec))
+            return fail(plan, Q2X_ERR_ARG, "vxyz, idx and sigma must be non-NULL");
         if (n_vert <= 0) return fail(plan, Q2X_ERR_ARG, "n_vert must be positive");
         if (n_leaves <= 0) return fail(plan, Q2X_ERR_ARG, "n_leaves must be positive");
         if (n_elem > ((int64_t)1 << 40)) return fail(plan, Q2X_ERR_ARG, "n_elem too large");
@@ -366,7 +294,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
 
     if (n_elem == 0) {
         if (!accumulate && n_leaves > 0) {
-            for (double* c : {coef0, coef1})
+            for (double* c : {coef0, coef1, coef2})
                 if (c) {
                     e = cudaMemsetAsync(c, 0, sizeof(double) * (size_t)n_leaves * np, plan->stream);
                     if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMemsetAsync");
@@ -376,13 +304,16 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     }
 
     const int prec = plan->prec;  // 0 FP64, 1 FP32-mixed
-    const int combo = combo_index(kind, dens, coef0 != nullptr, kind == q2x::KIND_TRI && coef1 != nullptr);
+    const int combo = combo_index(kind, dens, coef0 != nullptr, kind == q2x::KIND_TRI && coef1 != nullptr, vec);
+    const bool dbl = kind == q2x::KIND_TRI && coef1 != nullptr;
+    const int nacc = q2x::elem_outputs(kind, vec ? 4 : dbl ? 2 : 1);
     const int nv = kind + 2;
     const int bin = bin_index(plan->p_max);
     if (bin < 0) return fail(plan, Q2X_ERR_RANGE, "p_max %d above %d", plan->p_max, Q2X_P_MAX);
     const KernelEntry& ke = kTable[prec][combo][bin];
     const int wpc = prec ? q2x::elem_warps_per_cta<float>() : q2x::elem_warps_per_cta<double>();
-    const size_t smem = wpc * (prec ? q2x::warp_smem_bytes<float>(np) : q2x::warp_smem_bytes<double>(np));
+    const size_t smem =
+        wpc * (prec ? q2x::warp_smem_bytes<float>(np, nacc) : q2x::warp_smem_bytes<double>(np, nacc));
 
     int& occ = plan->occ_cache[prec][combo][bin];
     if (occ == 0) {
@@ -399,7 +330,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
 
     // workspace: slots, then per-leaf scale (FP32 without leaf_rho)
     const bool need_rho = prec == 1 && leaf_rho == nullptr;
-    const size_t slot_bytes = align_up(sizeof(double) * (size_t)n_ranges * 2 * 2 * np, 256);  // FP64 partials
+    const size_t slot_bytes = align_up(sizeof(double) * (size_t)n_ranges * 2 * nacc * np, 256);  // FP64 partials
     const size_t rho_bytes = need_rho ? align_up(sizeof(double) * (size_t)n_leaves, 256) : 0;
     const size_t bits_bytes = need_rho ? align_up(sizeof(int) * (size_t)n_leaves, 256) : 0;
     q2x_status st = ensure_ws(plan, slot_bytes + rho_bytes + bits_bytes);
@@ -439,14 +370,16 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     a.p_max = plan->p_max;
     a.np_max = np;
     a.coef[0] = coef0;
-    a.coef[1] = (kind == q2x::KIND_TRI) ? coef1 : nullptr;
+    a.coef[1] = (kind == q2x::KIND_TRI || vec) ? coef1 : nullptr;
+    a.coef[2] = vec ? coef2 : nullptr;
+    a.wvec = wvec;
+    a.nacc = nacc;
     a.accumulate = accumulate;
     a.norm = plan->norm;
     a.T = T;
     a.n_ranges = n_ranges;
     a.slots = reinterpret_cast<double*>(ws);
     a.err = plan->d_err;
-    a.raw = raw;
 
     const int grid = (int)((n_ranges + wpc - 1) / wpc);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -467,7 +400,10 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
         const int d_out = (kind == q2x::KIND_SEG) ? 1 : (kind == q2x::KIND_TET) ? 3 : (dens == Q2X_DENSITY_LINEAR ? 3 : 2);
         const int64_t nw = n_ranges - 1;
         const int fgrid = (int)((nw + 3) / 4);
-        q2x::q2x_fixup_kernel<<<fgrid, 128, 0, plan->stream>>>(a, kind + 1, d_out, d_out - 1);
+        if (vec)
+            q2x::q2x_fixup_kernel<<<fgrid, 128, 0, plan->stream>>>(a, d_out, d_out, d_out, kind + 1, kind + 1, kind + 1);
+        else
+            q2x::q2x_fixup_kernel<<<fgrid, 128, 0, plan->stream>>>(a, d_out, d_out - 1, d_out, kind + 1, 1, kind + 1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(plan, e, "fixup kernel launch");
         plan->launches += 1;
@@ -618,7 +554,7 @@ q2x_status q2x_reserve(q2x_plan_t plan, int64_t n_elem, int64_t n_leaves)
     const int np = (plan->p_max + 1) * (plan->p_max + 1);
     // worst case: one range per 32 elements; FP64 partials in both precisions
     const int64_t n_ranges = (n_elem + 31) / 32;
-    const size_t bytes = align_up(sizeof(double) * (size_t)n_ranges * 2 * 2 * np, 256) +
+    const size_t bytes = align_up(sizeof(double) * (size_t)n_ranges * 2 * 3 * np, 256) +
                          align_up(sizeof(double) * (size_t)n_leaves, 256) +
                          align_up(sizeof(int) * (size_t)n_leaves, 256);
     return ensure_ws(plan, bytes);
@@ -725,73 +661,11 @@ q2x_status q2x_segments_vector(q2x_plan_t plan, int64_t n_elem, int64_t n_vert, 
         }
         return Q2X_OK;
     }
-    check_leaf_off_kernel<<<(unsigned)((n_leaves + 1 + 255) / 256), 256, 0, plan->stream>>>(leaf_off, n_leaves, n_elem,
-                                                                                           plan->d_err);
-    plan->launches += 1;
-    // elements in chunks whose unfinished rows take at most 4 GiB (one chunk
-    // for a few million elements: every chunk pays a kernel tail)
-    const int64_t m_max = std::min<int64_t>(n_elem, std::max<int64_t>(1024, ((int64_t)1 << 32) / (8 * np)));
-    const bool need_rho = plan->prec == 1 && leaf_rho == nullptr;  // FP32 needs the leaf scale
-    const size_t b_rows = align_up(sizeof(double) * (size_t)m_max * np, 256);
-    const size_t b_ec = align_up(sizeof(double) * 3 * (size_t)m_max, 256);
-    const size_t b_er = align_up(sizeof(double) * (size_t)m_max, 256);
-    const size_t b_ep = align_up(sizeof(int32_t) * (size_t)m_max, 256);
-    const size_t b_idx = align_up(sizeof(int32_t) * 2 * (size_t)m_max, 256);
-    const size_t b_one = align_up(sizeof(double) * (size_t)m_max, 256);
-    const size_t b_rho = need_rho ? align_up(sizeof(double) * (size_t)n_leaves, 256) : 0;
-    const size_t b_bits = need_rho ? align_up(sizeof(int) * (size_t)n_leaves, 256) : 0;
-    unsigned char* tmp = nullptr;
-    e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), b_rows + b_ec + b_er + b_ep + b_idx + b_one + b_rho + b_bits,
-                        plan->stream);
-    if (e != cudaSuccess) return cuda_fail(plan, e, "cudaMallocAsync (vector rows)");
-    double* rows = reinterpret_cast<double*>(tmp);
-    double* ec = reinterpret_cast<double*>(tmp + b_rows);
-    double* er = reinterpret_cast<double*>(tmp + b_rows + b_ec);
-    int32_t* ep = reinterpret_cast<int32_t*>(tmp + b_rows + b_ec + b_er);
-    int32_t* idxc = reinterpret_cast<int32_t*>(tmp + b_rows + b_ec + b_er + b_ep);
-    double* ones = reinterpret_cast<double*>(tmp + b_rows + b_ec + b_er + b_ep + b_idx);
-    const double* rho = leaf_rho;
-    q2x_status st = Q2X_OK;
-    if (need_rho) {
-        double* r = reinterpret_cast<double*>(tmp + b_rows + b_ec + b_er + b_ep + b_idx + b_one);
-        int* bits = reinterpret_cast<int*>(tmp + b_rows + b_ec + b_er + b_ep + b_idx + b_one + b_rho);
-        e = cudaMemsetAsync(bits, 0, sizeof(int) * (size_t)n_leaves, plan->stream);
-        if (e == cudaSuccess) {
-            leaf_rho_kernel<<<(unsigned)((n_elem + 255) / 256), 256, 0, plan->stream>>>(
-                n_elem, n_vert, 2, vxyz, vxyz + n_vert, vxyz + 2 * n_vert, idx, n_leaves, leaf_off, leaf_c, bits);
-            rho_bits_to_double<<<(unsigned)((n_leaves + 255) / 256), 256, 0, plan->stream>>>(bits, r, n_leaves);
-            plan->launches += 2;
-            e = cudaGetLastError();
-        }
-        if (e != cudaSuccess) st = cuda_fail(plan, e, "leaf scale");
-        rho = r;
-    }
-    using C = q2x::Chain<q2x::KIND_SEG, q2x::DENS_CONST>;
-    const int64_t units = n_leaves * (int64_t)((np + 31) / 32);  // (leaf, 32-column group) warps
-    for (int64_t e0 = 0; st == Q2X_OK && e0 < n_elem; e0 += m_max) {
-        const int64_t m = std::min(m_max, n_elem - e0);
-        vector_gather_kernel<<<(unsigned)((m + 255) / 256), 256, 0, plan->stream>>>(
-            leaf_off, n_leaves, leaf_c, rho, leaf_p, idx, n_elem, e0, m, ec, rho ? er : nullptr,
-            leaf_p ? ep : nullptr, idxc, ones);
-        plan->launches += 1;
-        e = cudaGetLastError();
-        if (e != cudaSuccess) {
-            st = cuda_fail(plan, e, "vector gather launch");
-            break;
-        }
-        st = run_elements(plan, q2x::KIND_SEG, Q2X_DENSITY_CONST, m, n_vert, vxyz, idxc, ones, m, nullptr, ec,
-                          rho ? er : nullptr, leaf_p ? ep : nullptr, rows, nullptr, 0, /*raw=*/1);
-        if (st != Q2X_OK) break;
-        vector_reduce_kernel<<<(unsigned)((units + 7) / 8), 256, 0, plan->stream>>>(
-            rows, np, e0, e0 + m, n_elem, current, n_leaves, leaf_off, rho, leaf_p, plan->p_max, plan->norm,
-            C::D_OUT, q2x::KIND_SEG + 1, coef3, e0 == 0 ? accumulate : 1);
-        plan->launches += 1;
-        e = cudaGetLastError();
-        if (e != cudaSuccess) st = cuda_fail(plan, e, "vector reduce launch");
-    }
-    e = cudaFreeAsync(tmp, plan->stream);
-    if (st == Q2X_OK && e != cudaSuccess) st = cuda_fail(plan, e, "cudaFreeAsync");
-    return st;
+    // one pass over the segments: unit-density moments staged per round and
+    // reduced three times, weighted by the components (element kernel, vector mode)
+    const int64_t nl_np = n_leaves * (int64_t)np;
+    return run_elements(plan, q2x::KIND_SEG, Q2X_DENSITY_CONST, n_elem, n_vert, vxyz, idx, nullptr, n_leaves, leaf_off,
+                        leaf_c, leaf_rho, leaf_p, coef3, coef3 + nl_np, accumulate, current, coef3 + 2 * nl_np);
 }
 
 q2x_status q2x_leaf_reduce_weighted(q2x_plan_t plan, int64_t n_elem, int p, const double* elem, int n_w,

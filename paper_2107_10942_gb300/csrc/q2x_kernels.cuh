@@ -112,14 +112,16 @@ struct ElemArgs {
     const int32_t* leaf_p;    // NULL: p_max
     int p_max;
     int np_max;               // (p_max + 1)^2
-    double* coef[2];          // output layers (single, double); NULL = skip
+    double* coef[3];          // outputs: layers (single, double), or the three components of a
+                              // vector density; NULL = skip
+    const double* wvec;       // vector density: SoA 3 x n_elem components per element
+    int nacc;                 // output slots per leaf: 2 (layers) or 3 (vector components)
     int accumulate;
     int norm;                 // 0 COEFF, 1 MOMENT
     int64_t T;                // elements per warp range, multiple of 32
     int64_t n_ranges;
-    double* slots;            // [n_ranges][2 slots][2 layers][np_max] FP64 partial sums
+    double* slots;            // [n_ranges][2 slots][nacc outputs][np_max] FP64 partial sums
     unsigned* err;
-    int raw = 0;              // per-element mode: store the hat sums unfinished
 };
 
 // ------------------------------------------------------------- constants
@@ -481,8 +483,15 @@ __device__ __forceinline__ int64_t leaf_lower(const int64_t* __restrict__ off, i
 // the leaf's sums are finished.
 struct RangeCtx {
     int64_t w, e_lo, e_hi, L_first;
-    int d_out0, d_out1;        // hat depth of each layer's output level
-    int shift_n00, shift_n01;  // shift = s * (n + shift_n0 of the layer)
+    int d_out0, d_out1, d_out2;           // hat depth of each output's level
+    int shift_n00, shift_n01, shift_n02;  // shift = s * (n + shift_n0 of the output)
+    int nacc;                             // outputs per leaf
+    // (scalars with selects: an array indexed at run time would live in local memory)
+    __device__ __forceinline__ int d_out(int ly) const { return ly == 0 ? d_out0 : ly == 1 ? d_out1 : d_out2; }
+    __device__ __forceinline__ int shift_n0(int ly) const
+    {
+        return ly == 0 ? shift_n00 : ly == 1 ? shift_n01 : shift_n02;
+    }
 };
 
 // Running sum of one column over a leaf's rounds.  FP32: compensated (each
@@ -526,9 +535,7 @@ __device__ __forceinline__ void flush_value(const ElemArgs& a, const RangeCtx& r
         const int desc = col_desc(c);
         double v = 0.0;
         if ((desc & 31) < ((info >> 1) & 63))  // n <= p_leaf
-            v = a.raw ? acc.value()
-                      : finish_desc(acc.rounded(), a.norm, desc, ly ? rc.d_out1 : rc.d_out0,
-                                    ly ? rc.shift_n01 : rc.shift_n00, info >> 7);
+            v = finish_desc(acc.rounded(), a.norm, desc, rc.d_out(ly), rc.shift_n0(ly), info >> 7);
         double* dst = a.coef[ly] + (int64_t)L * a.np_max + c;
         if (a.accumulate)
             *dst += v;
@@ -536,7 +543,7 @@ __device__ __forceinline__ void flush_value(const ElemArgs& a, const RangeCtx& r
             *dst = v;
     } else {
         const int slot = (L == rc.L_first) ? 0 : 1;
-        a.slots[((rc.w * 2 + slot) * 2 + ly) * (int64_t)a.np_max + c] = acc.value();
+        a.slots[((rc.w * 2 + slot) * rc.nacc + ly) * (int64_t)a.np_max + c] = acc.value();
     }
 }
 
@@ -659,6 +666,83 @@ __device__ __forceinline__ void reduce_chunk(const ElemArgs& a, const RangeCtx& 
     }
 }
 
+// four consecutive values of a staged column (FP32 columns are 16-byte
+// aligned; FP64 columns only 8-byte aligned, LD = 33), and of a 16-byte
+// aligned shared array
+__device__ __forceinline__ void load4_col(const float* p, float (&v)[4])
+{
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+}
+__device__ __forceinline__ void load4_col(const double* p, double (&v)[4])
+{
+    v[0] = p[0], v[1] = p[1], v[2] = p[2], v[3] = p[3];
+}
+__device__ __forceinline__ void load4_aligned(const float* p, float (&v)[4]) { load4_col(p, v); }
+__device__ __forceinline__ void load4_aligned(const double* p, double (&v)[4])
+{
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+
+// Vector density (segments carrying a 3-component current): the staged rows
+// are the elements' unit-density moments, and component j of a leaf's sum is
+// the sum over its rows of w_j(row) * row, w_j the element's j-th component
+// (rowwt[j][32] in shared memory): the three components of Eq. (st3) from one
+// recursion pass.  Per column and component, each group of four rows gives a
+// weighted group sum (one multiply-add per row); the group sums are reduced
+// and flushed per leaf like reduce_chunk's, each component into its own
+// output (the column is re-read from shared memory per component, so the
+// group sums stay in registers).  Leaf mode only.
+template <typename T>
+__device__ __forceinline__ void reduce_chunk_vec(const ElemArgs& a, const RangeCtx& rc, const T* tile,
+                                                 LeafSum<T>* accb, const T* rowwt, const long long* rowleaf,
+                                                 const int* rowinfo, long long open_leaf, int open_info,
+                                                 unsigned gstart, int c0, int ncols)
+{
+    constexpr int LD = KCfg<T>::LD;
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int j = lane; j < ncols; j += 32) {
+        const int c = c0 + j;
+        const T* col = tile + j * LD;
+#pragma unroll 1
+        for (int q = 0; q < 3; ++q) {
+            if (a.coef[q] == nullptr) continue;
+            T s[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                T v[4], wq[4];
+                load4_col(col + 4 * g, v);
+                load4_aligned(rowwt + q * 32 + 4 * g, wq);  // the same address in every lane (broadcast)
+                s[g] = fma(wq[3], v[3], fma(wq[2], v[2], fma(wq[1], v[1], wq[0] * v[0])));
+            }
+            LeafSum<T> acc = accb[q * a.np_max + c];
+            if (gstart == 0) {
+                acc.add(((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
+            } else {
+                long long L = open_leaf;
+                int info = open_info;
+                unsigned mask = gstart;
+                int g0 = 0;
+                while (mask) {
+                    const int r = __ffs(mask) - 1;
+                    const int g1 = r >> 2;
+                    acc.add(tree8(s, g0, g1));
+                    flush_value<T>(a, rc, q, c, acc, L, info);
+                    acc.zero();
+                    L = rowleaf[r];
+                    info = rowinfo[r];
+                    g0 = g1;
+                    mask &= mask - 1;
+                }
+                acc.add(tree8(s, g0, 8));
+            }
+            accb[q * a.np_max + c] = acc;
+        }
+    }
+}
+
 // ---------------------------------------------------------- chain layout
 
 // Levels of the chain per element kind: the vertex of each level's stencil
@@ -709,7 +793,7 @@ struct Frame {
     T eu[3], ev[3];            // edges x2 - x1, x3 - x1 (triangles; eu only for segments)
 };
 
-template <typename T, int KIND, int DENS>
+template <typename T, int KIND, int DENS, bool UNIT = false>
 __device__ __forceinline__ void load_frame(const double* __restrict__ vx, const double* __restrict__ vy,
                                            const double* __restrict__ vz, const int32_t* __restrict__ idx,
                                            const double* __restrict__ sigma, int64_t n_elem, int64_t n_vert,
@@ -741,8 +825,8 @@ __device__ __forceinline__ void load_frame(const double* __restrict__ vx, const 
             }
             vid[k] = v;
         }
-        double dens[3] = {0.0, 0.0, 0.0};
-        if (active) {
+        double dens[3] = {UNIT ? 1.0 : 0.0, 0.0, 0.0};
+        if (active && !UNIT) {
             if (DENS == DENS_LINEAR) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) dens[k] = __ldg(sigma + vid[k]);
@@ -1152,15 +1236,25 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
     }
 }
 
+// Output slots per leaf of an element-kernel instantiation: the three
+// components of a vector density, the two layers when the double layer is
+// requested (slot 1; slot 0 is the single layer), else the single layer only.
+__host__ __device__ constexpr int elem_outputs(int kind, int outs)
+{
+    return (outs & 4) ? 3 : (kind == KIND_TRI && (outs & 2)) ? 2 : 1;
+}
+
 // Shared memory per warp: stage tile [2 layers][CHUNK][LD] of T, open-run sums
-// [2 layers][np_max] (LeafSum, 8 bytes), row leaves [32], row infos [32].
+// [nacc outputs][np_max] (LeafSum, 8 bytes), row leaves [32], row infos [32],
+// with a vector density the row weights [3][32] of T between the tile and the
+// sums (the tile's size keeps them 16-byte aligned).
 // (rounded up to 128 bytes so every warp's tile keeps the 16-byte alignment of
 // the 128-bit column loads)
 template <typename T>
-__host__ __device__ constexpr size_t warp_smem_bytes(int np_max)
+__host__ __device__ constexpr size_t warp_smem_bytes(int np_max, int nacc = 2)
 {
-    return (sizeof(T) * (size_t)(2 * KCfg<T>::CHUNK * KCfg<T>::LD) + sizeof(LeafSum<T>) * (size_t)(2 * np_max) +
-            sizeof(long long) * 32 + sizeof(int) * 32 + 127) / 128 * 128;
+    return (sizeof(T) * (size_t)(2 * KCfg<T>::CHUNK * KCfg<T>::LD + (nacc == 3 ? 96 : 0)) +
+            sizeof(LeafSum<T>) * (size_t)(nacc * np_max) + sizeof(long long) * 32 + sizeof(int) * 32 + 127) / 128 * 128;
 }
 
 // Resident CTAs per SM the element kernel is compiled for, which caps its
@@ -1172,7 +1266,7 @@ template <typename T, int P, int KIND, int DENS, int OUTS>
 __host__ __device__ constexpr int min_ctas()
 {
     if constexpr (sizeof(T) == 4) {
-        if (KIND == KIND_SEG && P <= 16) return 16;
+        if (KIND == KIND_SEG && OUTS == 1 && P <= 16) return 16;
         if (KIND == KIND_TRI && DENS == DENS_CONST && OUTS == 1 && P <= 8) return 16;
         if (KIND == KIND_TRI && DENS == DENS_CONST && OUTS == 1 && P <= 16) return 12;
         return 8;
@@ -1181,8 +1275,10 @@ __host__ __device__ constexpr int min_ctas()
     }
 }
 
-// OUTS: bit 0 = single layer, bit 1 = double layer (triangles); a compile-time
-// choice so each kernel holds exactly one copy of the degree loop.
+// OUTS: bit 0 = single layer, bit 1 = double layer (triangles), bit 2 = vector
+// density (segments: three current components weighting one unit-density
+// pass); a compile-time choice so each kernel holds exactly one copy of the
+// degree loop.
 template <typename T, int P, int KIND, int DENS, int OUTS>
 __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, KIND, DENS, OUTS>()))
     q2x_elem_kernel(const ElemArgs a)
@@ -1197,14 +1293,19 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
     const int64_t w = (int64_t)blockIdx.x * elem_warps_per_cta<T>() + wib;
     if (w >= a.n_ranges) return;
 
-    unsigned char* wsm = smem_raw + (size_t)wib * warp_smem_bytes<T>(a.np_max);
+    constexpr bool VEC = (OUTS & 4) != 0;  // vector density: three weighted outputs of one pass
+    constexpr int NACC = elem_outputs(KIND, OUTS);
+    unsigned char* wsm = smem_raw + (size_t)wib * warp_smem_bytes<T>(a.np_max, NACC);
     T* tile = reinterpret_cast<T*>(wsm);
-    LeafSum<T>* accb = reinterpret_cast<LeafSum<T>*>(tile + 2 * CH * LD);  // 2 CH LD sizeof(T) % 8 == 0
-    long long* rowleaf = reinterpret_cast<long long*>(accb + 2 * a.np_max);
+    T* rowwt = tile + 2 * CH * LD;  // vector density only: [3][32]
+    // 2 CH LD sizeof(T) and 96 sizeof(T) are multiples of 16
+    LeafSum<T>* accb = reinterpret_cast<LeafSum<T>*>(tile + 2 * CH * LD + (VEC ? 96 : 0));
+    long long* rowleaf = reinterpret_cast<long long*>(accb + NACC * a.np_max);
     int* rowinfo = reinterpret_cast<int*>(rowleaf + 32);
 
-    constexpr bool want0 = (OUTS & 1) != 0;
+    constexpr bool want0 = (OUTS & 1) != 0 || VEC;
     constexpr bool want1 = (KIND == KIND_TRI) && (OUTS & 2) != 0;
+    static_assert(NACC == (VEC ? 3 : want1 ? 2 : 1), "output slots");
     const bool per_elem = a.leaf_off == nullptr;
     const int np = a.np_max;
     const int pw = a.p_max;
@@ -1213,10 +1314,13 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
     rc.w = w;
     rc.e_lo = w * a.T;
     rc.e_hi = min(rc.e_lo + a.T, a.n_elem);
-    rc.d_out0 = C::D_OUT;
-    rc.d_out1 = C::D_OUT - 1;
-    rc.shift_n00 = KIND + 1;
-    rc.shift_n01 = 1;
+    // output 1 is the double layer (one hat degree less, scale exponent n + 1),
+    // or a vector component (the single layer's constants)
+    rc.d_out0 = rc.d_out2 = C::D_OUT;
+    rc.d_out1 = VEC ? C::D_OUT : C::D_OUT - 1;
+    rc.shift_n00 = rc.shift_n02 = KIND + 1;
+    rc.shift_n01 = VEC ? KIND + 1 : 1;
+    rc.nacc = NACC;
 
     int64_t L_last;
     if (per_elem) {
@@ -1227,7 +1331,7 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
         L_last = leaf_search(a.leaf_off, rc.L_first, a.n_leaves - 1, rc.e_hi - 1);
     }
 
-    for (int k = lane; k < 2 * np; k += 32) accb[k].zero();
+    for (int k = lane; k < NACC * np; k += 32) accb[k].zero();
 
     // zero the coefficients of empty leaves [La, Lb) (overwrite mode)
     auto zero_leaves = [&](int64_t La, int64_t Lb) {
@@ -1236,8 +1340,14 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
         for (int64_t L = La; L < Lb; ++L)
 #pragma unroll 1
             for (int c = lane; c < np; c += 32) {
-                if (want0) a.coef[0][L * np + c] = 0.0;
-                if (want1) a.coef[1][L * np + c] = 0.0;
+                if (VEC) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        if (a.coef[q]) a.coef[q][L * np + c] = 0.0;
+                } else {
+                    if (want0) a.coef[0][L * np + c] = 0.0;
+                    if (want1) a.coef[1][L * np + c] = 0.0;
+                }
             }
     };
     if (!per_elem) {
@@ -1336,15 +1446,33 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
         const int last = 31 - __clz(__ballot_sync(0xffffffffu, active));
         rowleaf[lane] = (long long)L;
         rowinfo[lane] = info;
+        if constexpr (VEC) {
+            // this lane's element's current components: the row weights (a
+            // non-finite component zeroes the whole segment)
+            double wq[3];
+            bool fin = true;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                wq[q] = active ? __ldg(a.wvec + (int64_t)q * a.n_elem + e) : 0.0;
+                fin = fin && finite_bits(wq[q]);
+            }
+            if (!fin) errbits |= 2u;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) rowwt[q * 32 + lane] = fin ? (T)wq[q] : T(0);
+        }
         __syncwarp();
 
         Frame<T, NL> F;
-        load_frame<T, KIND, DENS>(a.vx, a.vy, a.vz, a.idx, a.sigma, a.n_elem, a.n_vert, e, active, cx, cy, cz, sexp,
-                                  errbits, pL, F);
+        load_frame<T, KIND, DENS, VEC>(a.vx, a.vy, a.vz, a.idx, a.sigma, a.n_elem, a.n_vert, e, active, cx, cy, cz,
+                                       sexp, errbits, pL, F);
         if (errbits) atomicOr(a.err, errbits);
-        run_chain<T, P, KIND, DENS, OUTS, true>(F, pw, tile, lane, [&](int c0, int ncols) {
-            reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, gstart, n_taken, c0, ncols,
-                            want0, want1, per_elem);
+        run_chain<T, P, KIND, DENS, VEC ? 1 : OUTS, true>(F, pw, tile, lane, [&](int c0, int ncols) {
+            if constexpr (VEC)
+                reduce_chunk_vec<T>(a, rc, tile, accb, rowwt, rowleaf, rowinfo, open_leaf, open_info, gstart, c0,
+                                    ncols);
+            else
+                reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, gstart, n_taken, c0,
+                                ncols, want0, want1, per_elem);
         });
         // the run open at the end of this round
         open_leaf = rowleaf[last];
@@ -1355,8 +1483,8 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
 
     // ---- flush the run left open at the end of the range
 #pragma unroll 1
-    for (int ly = 0; ly < 2 && !per_elem; ++ly) {
-        if ((ly == 0 && !want0) || (ly == 1 && !want1)) continue;
+    for (int ly = 0; ly < NACC && !per_elem; ++ly) {
+        if (VEC ? a.coef[ly] == nullptr : ((ly == 0 && !want0) || (ly == 1 && !want1) || ly == 2)) continue;
 #pragma unroll 1
         for (int c = lane; c < np; c += 32)
             flush_value<T>(a, rc, ly, c, accb[ly * np + c], open_leaf, open_info);
@@ -1367,7 +1495,7 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
 // per range boundary w (1 <= w < n_ranges): the leaf L containing element w*T,
 // handled here iff w is the last range L touches.  The FP64 partials are summed
 // in range order (compensated), then scaled like a complete run.
-static __global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d1)
+static __global__ void q2x_fixup_kernel(const ElemArgs a, int d0, int d1, int d2, int s0, int s1, int s2)
 {
     const int lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) + 1;
@@ -1388,13 +1516,13 @@ static __global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d
     }
     const int np = a.np_max;
     const double* slots = a.slots;
-    for (int ly = 0; ly < 2; ++ly) {
+    for (int ly = 0; ly < a.nacc; ++ly) {
         if (a.coef[ly] == nullptr) continue;
         for (int c = lane; c < np; c += 32) {
-            double sum = slots[((wf * 2 + slot_first) * 2 + ly) * (int64_t)np + c];
+            double sum = slots[((wf * 2 + slot_first) * a.nacc + ly) * (int64_t)np + c];
             double comp = 0.0;
             for (int64_t ww = wf + 1; ww <= w; ++ww) {
-                const double x = slots[((ww * 2 + 0) * 2 + ly) * (int64_t)np + c];
+                const double x = slots[((ww * 2 + 0) * a.nacc + ly) * (int64_t)np + c];
                 // Kahan-Babuska (Neumaier) step
                 const double t = sum + x;
                 if (fabs(sum) >= fabs(x))
@@ -1406,7 +1534,8 @@ static __global__ void q2x_fixup_kernel(const ElemArgs a, int dim, int d0, int d
             sum += comp;
             const int desc = col_desc(c);
             const double v = ((desc & 31) <= pl)
-                                 ? finish_desc(sum, a.norm, desc, ly == 0 ? d0 : d1, ly == 0 ? dim : 1, s)
+                                 ? finish_desc(sum, a.norm, desc, ly == 0 ? d0 : ly == 1 ? d1 : d2,
+                                               ly == 0 ? s0 : ly == 1 ? s1 : s2, s)
                                  : 0.0;
             double* dst = a.coef[ly] + L * np + c;
             if (a.accumulate)
@@ -1436,7 +1565,7 @@ cudaError_t elem_smem_attribute()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < kMaxDevices && done[dev]) return cudaSuccess;
-    const size_t smem_max = elem_warps_per_cta<T>() * warp_smem_bytes<T>((P + 1) * (P + 1));
+    const size_t smem_max = elem_warps_per_cta<T>() * warp_smem_bytes<T>((P + 1) * (P + 1), elem_outputs(KIND, OUTS));
     e = cudaFuncSetAttribute(q2x_elem_kernel<T, P, KIND, DENS, OUTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_max);
     if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) done[dev] = 1;

@@ -171,6 +171,9 @@ extern "C" q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precis
     a.np_max = np;
     a.coef[0] = coef_single;
     a.coef[1] = coef_double;
+    a.coef[2] = nullptr;
+    a.wvec = nullptr;
+    a.nacc = q2x::elem_outputs(q2x::KIND_TRI, coef_double ? 2 : 1);
     a.accumulate = accumulate;
     a.norm = (int)norm;
     a.T = T;
@@ -179,14 +182,15 @@ extern "C" q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precis
     a.err = err;
 
     const int wpc = prec ? q2x::elem_warps_per_cta<float>() : q2x::elem_warps_per_cta<double>();
-    const size_t smem = wpc * (prec ? q2x::warp_smem_bytes<float>(np) : q2x::warp_smem_bytes<double>(np));
+    const size_t smem =
+        wpc * (prec ? q2x::warp_smem_bytes<float>(np, a.nacc) : q2x::warp_smem_bytes<double>(np, a.nacc));
     const int grid = (int)((n_ranges + wpc - 1) / wpc);
     const int outs = (coef_single ? 1 : 0) | (coef_double ? 2 : 0);
     if (kTri[prec][density][outs - 1][bin](a, grid, smem, stream) != cudaSuccess) return Q2X_ERR_CUDA;
     if (n_ranges > 1) {
         const int d_out = (density == Q2X_DENSITY_LINEAR) ? 3 : 2;
         const int fgrid = (int)((n_ranges - 1 + 3) / 4);
-        q2x::q2x_fixup_kernel<<<fgrid, 128, 0, stream>>>(a, 2, d_out, d_out - 1);
+        q2x::q2x_fixup_kernel<<<fgrid, 128, 0, stream>>>(a, d_out, d_out - 1, d_out, 2, 1, 2);
         if (cudaGetLastError() != cudaSuccess) return Q2X_ERR_CUDA;
     }
     return Q2X_OK;

@@ -20,7 +20,7 @@ struct q2x_plan_s {
     unsigned* h_err = nullptr;  // pinned
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    int occ_cache[2][8][5] = {};  // [precision][element combo][capacity bin]
+    int occ_cache[2][9][5] = {};  // [precision][element combo][capacity bin]
     int timing = 0;
     std::vector<cudaEvent_t> ev_pool;                            // idle events
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded pairs

@@ -132,3 +132,23 @@ def test_leaf_reduce_weighted(q2x):
         assert np.array_equal(acc, got + 2.0)
     with pytest.raises(ValueError):  # at most four weight rows
         plan.leaf_reduce_weighted(T(elem), p, T(off), T(np.zeros((5, n))))
+
+
+def test_vector_nonfinite_component_contributes_zero(q2x):
+    """A non-finite current component sets the device error word's
+    non-finite bit and its segment contributes zero to all three
+    components; the other segments are unaffected."""
+    p = 8
+    prob, cur = filament_problem(p)
+    bad = cur.copy()
+    bad[1, 5] = np.nan
+    zeroed = cur.copy()
+    zeroed[:, 5] = 0.0
+    plan = q2x.Plan(p, precision="fp64")
+    args = (T(prob["vxyz"]), T(prob["idx"]))
+    leaf = (T(prob["leaf_off"]), T(prob["leaf_c"]), T(prob["leaf_rho"]))
+    ref = plan.segments_vector(*args, T(zeroed), *leaf)
+    plan.sync()
+    got = plan.segments_vector(*args, T(bad), *leaf)
+    assert plan.device_errors() & 2
+    assert torch.equal(got, ref)
