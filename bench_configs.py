@@ -194,7 +194,15 @@ def run_icosphere_l3(args, dev):
     coef = torch.empty((1, (p + 1) ** 2), dtype=torch.float64, device=dev)
     fn = lambda: plan.triangles(d["vxyz"], d["idx"], d["sigma"], d["leaf_off"], d["leaf_c"], d["leaf_rho"], None,
                                 coef_single=coef)
-    ms = _time(fn, args.steps, args.warmup, flush, stream)
+    # the step (check, element kernel, fix-up) as one CUDA graph, so that host
+    # launch gaps do not enter the device time of this small problem
+    g = plan.capture(fn)
+    ms = _time(g.replay, args.steps, args.warmup, flush, stream)
+    plan.set_kernel_timing(True)
+    plan.kernel_timing()
+    _time(fn, args.steps, 0, flush, stream)
+    kms, kn = plan.kernel_timing()
+    plan.set_kernel_timing(False)
     got = coef.cpu().numpy()
     plan.sync()
     t0 = time.perf_counter()
@@ -211,7 +219,11 @@ def run_icosphere_l3(args, dev):
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "icosphere-L3: %d triangles, one expansion about the origin, p=10, single layer, "
                                   "constant density" % n_elem,
-                      "note": "latency-bound: one leaf, one warp range per 32 triangles"},
+                      "step": "one CUDA-graph replay (check, element kernel, fix-up)", "kernel_ms": kms / max(kn, 1),
+                      "note": "latency-bound: 40 warps of 32 triangles, one per SM sub-partition; each runs its "
+                              "round's FP64 chain alone on its sub-partition's FP64 pipe (about 2,000 FP64 "
+                              "instructions of 64 pipe cycles each), so the kernel cannot take less than about "
+                              "0.06 ms however many SMs are idle"},
            "errors_vs_oracle": {"fp64": _norm_err(got, ref, prob["leaf_rho"], p)},
            "cpu_baseline": {"value": per_step / dt, "unit": UNIT, "kind": "oracle", "cores": orc.max_threads(),
                             "sample": "the whole workload, %d repetitions" % reps}})

@@ -52,11 +52,12 @@ struct BatchArgs {
 
 constexpr int BATCH_WARPS = 4;
 
-// stage tile [CHUNK][LD] of T, then the tile's column sums [np_max] (LeafSum)
+// stage tile [2 CHUNK][LD] of T (single-layer passes stage twice CHUNK
+// columns per reduction), then the tile's column sums [np_max] (LeafSum)
 template <typename T>
 __host__ __device__ constexpr size_t batch_warp_smem_bytes(int np_max)
 {
-    return (sizeof(T) * (size_t)(KCfg<T>::CHUNK * KCfg<T>::LD) + sizeof(LeafSum<T>) * (size_t)np_max + 127) /
+    return (sizeof(T) * (size_t)(2 * KCfg<T>::CHUNK * KCfg<T>::LD) + sizeof(LeafSum<T>) * (size_t)np_max + 127) /
            128 * 128;
 }
 
@@ -90,7 +91,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& 
             Frame<T, C::NL> F;
             load_frame<T, KIND, DENS>(K.vx, K.vy, K.vz, K.idx, K.sigma, K.n_elem, K.n_vert, e, active, cx, cy,
                                       cz, sexp, errbits, pl, F);
-            run_chain<T, P, KIND, DENS, 1>(F, pL, tile, lane, [&](int c0, int ncols) {
+            run_chain<T, P, KIND, DENS, 1, true>(F, pL, tile, lane, [&](int c0, int ncols) {
                 // each round's 32 rows summed pairwise, the rounds accumulated
                 // in a LeafSum (compensated in FP32)
                 for (int j = lane; j < ncols; j += 32) accb[c0 + j].add(sum_rows32(tile + j * LD));
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, 2) q2x_batch_kernel(const Ba
     const int wib = threadIdx.x >> 5;
     unsigned char* wsm = smem_raw + (size_t)wib * batch_warp_smem_bytes<T>(b.np_max);
     T* tile = reinterpret_cast<T*>(wsm);
-    LeafSum<T>* accb = reinterpret_cast<LeafSum<T>*>(tile + KCfg<T>::CHUNK * KCfg<T>::LD);  // CHUNK LD sizeof(T) % 8 == 0
+    LeafSum<T>* accb = reinterpret_cast<LeafSum<T>*>(tile + 2 * KCfg<T>::CHUNK * KCfg<T>::LD);  // 2 CHUNK LD sizeof(T) % 8 == 0
 #pragma unroll 1
     while (true) {
         unsigned long long ti = 0;
