@@ -63,10 +63,10 @@ DEFAULT_WORKLOAD = "sphere-L9-const"
 # 4 x FFMA2 + 2 x FFMA + 2 x FADD2 + FADD + FMUL (per-opcode thread counts:
 # the packed instructions are not in the FFMA/FADD class counters).
 KERNEL_COUNTERS = {
-    ("sphere-L9-const", "fp64"): dict(traffic=236734208 + 130404096, executed_flops=35717877081),
-    ("sphere-L9-const", "fp32"): dict(traffic=221895680 + 112655360, executed_flops=41174200000),
-    ("sphere-L7-linear", "fp64"): dict(traffic=9746944 + 40769280, executed_flops=2859759419),
-    ("sphere-L7-linear", "fp32"): dict(traffic=9387776 + 256, executed_flops=3403620000),
+    ("sphere-L9-const", "fp64"): {},
+    ("sphere-L9-const", "fp32"): {},
+    ("sphere-L7-linear", "fp64"): {},
+    ("sphere-L7-linear", "fp32"): {},
 }
 COUNTER_SOURCE = "ncu --set full capture of one launch of this kernel on this workload"
 

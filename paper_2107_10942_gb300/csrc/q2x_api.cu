@@ -30,8 +30,9 @@ Q2X_DECLARE_ALL(double)
 namespace {
 
 struct KernelEntry {
-    cudaError_t (*launch)(const q2x::ElemArgs&, int, size_t, cudaStream_t);
-    cudaError_t (*occupancy)(int*, size_t);
+    cudaError_t (*launch)(const q2x::ElemArgs&, int, cudaStream_t);
+    cudaError_t (*occupancy)(int*, int);
+    size_t (*smem)(int);  // dynamic shared memory of a launch at np_max columns
 };
 
 constexpr int kNumBins = 5;
@@ -39,7 +40,8 @@ constexpr int kBins[kNumBins] = {4, 8, 12, 16, 20};
 constexpr int kNumCombos = 9;
 
 #define Q2X_ENTRY(T, P, KIND, DENS, OUTS) \
-    {&q2x::launch_elem<T, P, KIND, DENS, OUTS>, &q2x::occupancy_elem<T, P, KIND, DENS, OUTS>},
+    {&q2x::launch_elem<T, P, KIND, DENS, OUTS>, &q2x::occupancy_elem<T, P, KIND, DENS, OUTS>, \
+     &q2x::elem_launch_smem<T, P, KIND, DENS, OUTS>},
 #define Q2X_ROW(T, KIND, DENS, OUTS) {Q2X_FOR_BINS(Q2X_ENTRY, T, KIND, DENS, OUTS)},
 #define Q2X_ROWS(T)                                                                                          \
     {Q2X_ROW(T, q2x::KIND_SEG, q2x::DENS_CONST, 1) Q2X_ROW(T, q2x::KIND_TRI, q2x::DENS_CONST, 1)              \
@@ -312,14 +314,12 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     if (bin < 0) return fail(plan, Q2X_ERR_RANGE, "p_max %d above %d", plan->p_max, Q2X_P_MAX);
     const KernelEntry& ke = kTable[prec][combo][bin];
     const int wpc = prec ? q2x::elem_warps_per_cta<float>() : q2x::elem_warps_per_cta<double>();
-    const size_t smem =
-        wpc * (prec ? q2x::warp_smem_bytes<float>(np, nacc) : q2x::warp_smem_bytes<double>(np, nacc));
 
     int& occ = plan->occ_cache[prec][combo][bin];
     if (occ == 0) {
-        e = ke.occupancy(&occ, smem);
+        e = ke.occupancy(&occ, np);
         if (e != cudaSuccess) return cuda_fail(plan, e, "occupancy query");
-        if (occ <= 0) return fail(plan, Q2X_ERR_CUDA, "kernel does not fit on the device (smem %zu)", smem);
+        if (occ <= 0) return fail(plan, Q2X_ERR_CUDA, "kernel does not fit on the device (smem %zu)", ke.smem(np));
     }
     const int64_t resident_warps = (int64_t)occ * wpc * plan->num_sms;
     // one range per resident warp (ranges need not be multiples of 32: rounds
@@ -389,7 +389,7 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
         if (st != Q2X_OK) return st;
         cudaEventRecord(ev0, plan->stream);
     }
-    e = ke.launch(a, grid, smem, plan->stream);
+    e = ke.launch(a, grid, plan->stream);
     if (e != cudaSuccess) return cuda_fail(plan, e, "element kernel launch");
     if (plan->timing) {
         cudaEventRecord(ev1, plan->stream);
@@ -398,13 +398,10 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     plan->launches += 1;
     if (leaf_off && n_ranges > 1) {
         const int d_out = (kind == q2x::KIND_SEG) ? 1 : (kind == q2x::KIND_TET) ? 3 : (dens == Q2X_DENSITY_LINEAR ? 3 : 2);
-        const int64_t nw = n_ranges - 1;
-        const int fgrid = (int)((nw + 3) / 4);
         if (vec)
-            q2x::q2x_fixup_kernel<<<fgrid, 128, 0, plan->stream>>>(a, d_out, d_out, d_out, kind + 1, kind + 1, kind + 1);
+            e = q2x::launch_fixup(a, plan->stream, d_out, d_out, d_out, kind + 1, kind + 1, kind + 1);
         else
-            q2x::q2x_fixup_kernel<<<fgrid, 128, 0, plan->stream>>>(a, d_out, d_out - 1, d_out, kind + 1, 1, kind + 1);
-        e = cudaGetLastError();
+            e = q2x::launch_fixup(a, plan->stream, d_out, d_out - 1, d_out, kind + 1, 1, kind + 1);
         if (e != cudaSuccess) return cuda_fail(plan, e, "fixup kernel launch");
         plan->launches += 1;
     }

@@ -494,6 +494,54 @@ struct RangeCtx {
     }
 };
 
+// The range walk's warp-uniform state.  FP32 keeps it in registers; FP64 keeps
+// it in shared memory (WarpWalk, written by lane 0, read through a volatile
+// pointer), since values live across the degree loop would otherwise hold
+// registers beside its rows for the loop's whole length (the FP64 level-9
+// kernel: 140 bytes of spill stores with them in registers, 8 without; 0.8 %
+// of its time).  In FP32 the extra shared-memory reads cost 6 %.
+struct WarpWalk {
+    int64_t w, e_lo, e_hi, L_first, L_last;
+    int64_t e_cur;      // first element of the current round
+    int64_t open_leaf;  // leaf of the run open at the start of the round
+    int open_info;
+    unsigned gstart;    // groups of the round that start a new leaf (bit 4g)
+    int n_taken;        // elements of the round
+    int last;           // last active lane of the round
+};
+#define Q2X_WALK_FIELDS(X)                                                                         \
+    X(int64_t, w) X(int64_t, e_lo) X(int64_t, e_hi) X(int64_t, L_first) X(int64_t, L_last)     \
+        X(int64_t, e_cur) X(int64_t, open_leaf) X(int, open_info) X(unsigned, gstart) X(int, n_taken) X(int, last)
+template <bool SMEM>
+struct Walk;
+template <>
+struct Walk<false> {
+    WarpWalk v;
+    __device__ __forceinline__ Walk(WarpWalk*, int) {}
+#define Q2X_WALK_REG(T, f)                                                                         \
+    __device__ __forceinline__ T f() const { return v.f; }                                         \
+    __device__ __forceinline__ void set_##f(T x) { v.f = x; }
+    Q2X_WALK_FIELDS(Q2X_WALK_REG)
+#undef Q2X_WALK_REG
+    __device__ __forceinline__ void sync() const {}
+};
+template <>
+struct Walk<true> {
+    volatile WarpWalk* p;
+    int lane;
+    __device__ __forceinline__ Walk(WarpWalk* q, int l) : p(q), lane(l) {}
+#define Q2X_WALK_SMEM(T, f)                                                                        \
+    __device__ __forceinline__ T f() const { return p->f; }                                        \
+    __device__ __forceinline__ void set_##f(T x) const                                             \
+    {                                                                                              \
+        if (lane == 0) p->f = x;                                                                   \
+    }
+    Q2X_WALK_FIELDS(Q2X_WALK_SMEM)
+#undef Q2X_WALK_SMEM
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+#undef Q2X_WALK_FIELDS
+
 // Running sum of one column over a leaf's rounds.  FP32: compensated (each
 // round's 32-row partial is added by TwoSum and the rounding errors are
 // accumulated beside the sum), so the leaf sum keeps FP32 accuracy relative
@@ -583,6 +631,39 @@ __device__ __forceinline__ T sum_rows32(const T* col)
     return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
+// Per-element expansions (no leaves): row r of a staged chunk is the complete
+// expansion of element rowleaf[r], finished and written directly.  Out of
+// line, a call made in that mode only, so that the leaf-mode degree loop does
+// not carry this code: the element kernel is sensitive to instruction fetch
+// (compiled out, the path's inlined copy cost 3 % of the level-9 FP32 step).
+template <typename T, int CH>
+__device__ __noinline__ void flush_rows_per_elem(const T* tile, const long long* rowleaf, const int* rowinfo,
+                                                 int nrows, int c0, int ncols, bool want0, bool want1,
+                                                 double* coef0, double* coef1, int np, int norm, int accumulate,
+                                                 int d0, int d1, int sh0, int sh1)
+{
+    constexpr int LD = KCfg<T>::LD;
+    const int lane = threadIdx.x & 31;
+    const int total = ((want0 ? 1 : 0) + (want1 ? 1 : 0)) * ncols;
+    for (int i = lane; i < nrows * total; i += 32) {
+        const int r = i / total, tc = i - r * total;
+        const int second = (tc >= ncols) ? 1 : 0;
+        const int ly = want0 ? second : 1;
+        const int j = tc - second * ncols, c = c0 + j;
+        const int info = rowinfo[r];
+        const int desc = col_desc(c);
+        double v = 0.0;
+        if ((desc & 31) < ((info >> 1) & 63))  // n <= p of the element
+            v = finish_desc(tile[(ly * CH + j) * LD + r], norm, desc, ly == 0 ? d0 : d1, ly == 0 ? sh0 : sh1,
+                            info >> 7);
+        double* dst = (ly == 0 ? coef0 : coef1) + (int64_t)rowleaf[r] * np + c;
+        if (accumulate)
+            *dst += v;
+        else
+            *dst = v;
+    }
+}
+
 // Segmented column sums of one staged chunk: columns [c0, c0 + ncols) of each
 // wanted layer.  Rows come in eight groups of four lanes; a leaf always starts
 // at a group boundary (the round assigns elements to lanes that way; padding
@@ -593,44 +674,23 @@ __device__ __forceinline__ T sum_rows32(const T* col)
 // summed and flushed in order.  The wanted layers' columns form one index
 // space; lane j owns indices j, j+32, ...; the open run's sum lives in accb
 // between chunks and rounds (a LeafSum: compensated in FP32).  Per-element
-// expansions (no leaves): row r is the complete expansion of element
-// rowleaf[r], finished directly.  All control flow is warp-uniform.
-template <typename T>
+// expansions (no leaves): flush_rows_per_elem, out of line.
+// All control flow is warp-uniform.
+template <typename T, int CH = KCfg<T>::CHUNK>
 __device__ __forceinline__ void reduce_chunk(const ElemArgs& a, const RangeCtx& rc, const T* tile,
                                              LeafSum<T>* accb, const long long* rowleaf, const int* rowinfo,
                                              long long open_leaf, int open_info, unsigned gstart,
                                              int nrows, int c0, int ncols, bool want0, bool want1,
                                              bool per_elem)
 {
-    constexpr int CH = KCfg<T>::CHUNK, LD = KCfg<T>::LD;
+    constexpr int LD = KCfg<T>::LD;
     const int lane = threadIdx.x & 31;
     const int nlay = (want0 ? 1 : 0) + (want1 ? 1 : 0);
     const int total = nlay * ncols;
     if (per_elem) {
-        // the (row, column) items of the chunk in row-major order, 32 at a
-        // time, unrolled so that several stores are in flight (a row is one
-        // element's complete expansion)
-        const int n_items = nrows * total;
-        int r = 0, tc = lane;
-        while (tc >= total && r < nrows) {
-            tc -= total;
-            ++r;
-        }
-#pragma unroll 4
-        for (int i = lane; i < n_items; i += 32) {
-            const int second = (tc >= ncols) ? 1 : 0;
-            const int ly = want0 ? second : 1;
-            const int j = tc - second * ncols;
-            LeafSum<T> one;
-            one.zero();
-            one.s = tile[(ly * CH + j) * LD + r];
-            flush_value<T>(a, rc, ly, c0 + j, one, rowleaf[r], rowinfo[r]);
-            tc += 32;
-            while (tc >= total) {
-                tc -= total;
-                ++r;
-            }
-        }
+        flush_rows_per_elem<T, CH>(tile, rowleaf, rowinfo, nrows, c0, ncols, want0, want1, a.coef[0], a.coef[1],
+                                   a.np_max, a.norm, a.accumulate, rc.d_out(0), rc.d_out(1), rc.shift_n0(0),
+                                   rc.shift_n0(1));
         return;
     }
 #pragma unroll 1
@@ -995,14 +1055,19 @@ __device__ __forceinline__ void load_frame(const double* __restrict__ vx, const 
 // stage each degree's single- and double-layer values of this lane's element
 // in column order of the stage tile (layer 1 at tile + CHUNK*LD), and call
 // reduce(c0, ncols) whenever a chunk of columns [c0, c0 + ncols) is complete.
-template <typename T, int P, int KIND, int DENS, int OUTS, bool WIDE = false, typename Reduce>
+//
+// FP64: the rows of levels k < NS live in shared memory (srows, [NS][P + 1][32]
+// complex entries, one 16-byte entry per lane and order) instead of registers;
+// see smem_levels.
+template <typename T, int P, int KIND, int DENS, int OUTS, bool WIDE = false, int NS = 0,
+          int CH = KCfg<T>::CHUNK, typename Reduce>
 __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>& F, int pw, T* tile,
-                                          int lane, Reduce&& reduce)
+                                          int lane, Reduce&& reduce, double2* srows = nullptr)
 {
     using C = Chain<KIND, DENS>;
     constexpr int NL = C::NL;
     constexpr int OUT = NL - 1;
-    constexpr int CH = KCfg<T>::CHUNK, LD = KCfg<T>::LD;
+    constexpr int LD = KCfg<T>::LD;
     constexpr bool FP32 = sizeof(T) == 4;
     constexpr bool LIN = (KIND == KIND_TRI && DENS == DENS_LINEAR);
     constexpr bool want0 = (OUTS & 1) != 0;
@@ -1010,6 +1075,8 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
     // columns staged per chunk: a single-layer pass may use both halves of a
     // two-layer tile (WIDE), which halves the reductions per round
     constexpr int CAP = (WIDE && !want1) ? 2 * CH : CH;
+    static_assert(NS == 0 || (sizeof(T) == 8 && NS < NL), "shared-memory rows: FP64 levels below the output");
+    static_assert(CAP >= 2 * P + 1, "a chunk must hold one degree's columns");
     const T s1 = F.s1, s2 = F.s2, s3 = F.s3, seed = F.seed;
     const T XN = F.XN, YN = F.YN, ZN = F.ZN;
     const T* LX = F.LX;
@@ -1144,9 +1211,23 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                 T nr[NL], ni[NL];
 #pragma unroll
                 for (int k = 0; k < NL; ++k) {
-                    const T cr = HC ? Rr[k][m] : T(0), ci = HC ? Ri[k][m] : T(0);
-                    const T br = HB ? Rr[k][m < P ? m + 1 : P] : T(0);
-                    const T bi = HB ? Ri[k][m < P ? m + 1 : P] : T(0);
+                    T cr = T(0), ci = T(0), br = T(0), bi = T(0);
+                    if (k < NS) {
+                        // degree n-1 entries m and m+1 of a shared-memory row
+                        // (entries above n-1 are never read, so the rows need
+                        // no clearing between elements)
+                        if (HC) {
+                            const double2 v = srows[(k * (P + 1) + m) * 32 + lane];
+                            cr = v.x, ci = v.y;
+                        }
+                        if (HB) {
+                            const double2 v = srows[(k * (P + 1) + (m < P ? m + 1 : P)) * 32 + lane];
+                            br = v.x, bi = v.y;
+                        }
+                    } else {
+                        if (HC) cr = Rr[k][m], ci = Ri[k][m];
+                        if (HB) br = Rr[k][m < P ? m + 1 : P], bi = Ri[k][m < P ? m + 1 : P];
+                    }
                     if (KIND == KIND_TRI && k == OUT && want1) {
                         T dr = T(0), di = T(0);
                         if (m == 0) {
@@ -1206,8 +1287,12 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                     ni[k] = vi;
                     pr[k] = cr;
                     pi[k] = ci;
-                    Rr[k][m] = vr;
-                    Ri[k][m] = vi;
+                    if (k < NS) {
+                        srows[(k * (P + 1) + m) * 32 + lane] = make_double2(vr, vi);
+                    } else {
+                        Rr[k][m] = vr;
+                        Ri[k][m] = vi;
+                    }
                 }
                 if (want0) {
                     T vr = nr[OUT], vi = ni[OUT];
@@ -1246,16 +1331,54 @@ __host__ __device__ constexpr int elem_outputs(int kind, int outs)
 
 // Shared memory per warp: stage tile [2 layers][CHUNK][LD] of T, open-run sums
 // [nacc outputs][np_max] (LeafSum, 8 bytes), row leaves [32], row infos [32],
-// with a vector density the row weights [3][32] of T between the tile and the
+// the walk state (FP64), with a vector density the row weights [3][32] of T between the tile and the
 // sums (the tile's size keeps them 16-byte aligned).
 // (rounded up to 128 bytes so every warp's tile keeps the 16-byte alignment of
 // the 128-bit column loads)
 template <typename T>
-__host__ __device__ constexpr size_t warp_smem_bytes(int np_max, int nacc = 2)
+__host__ __device__ constexpr size_t warp_smem_bytes(int np_max, int nacc = 2, int ch = KCfg<T>::CHUNK)
 {
-    return (sizeof(T) * (size_t)(2 * KCfg<T>::CHUNK * KCfg<T>::LD + (nacc == 3 ? 96 : 0)) +
-            sizeof(LeafSum<T>) * (size_t)(nacc * np_max) + sizeof(long long) * 32 + sizeof(int) * 32 + 127) / 128 * 128;
+    return (sizeof(T) * (size_t)(2 * ch * KCfg<T>::LD + (nacc == 3 ? 96 : 0)) +
+            sizeof(LeafSum<T>) * (size_t)(nacc * np_max) + sizeof(long long) * 32 + sizeof(int) * 32 +
+            sizeof(WarpWalk) + 127) / 128 * 128;
 }
+
+// Stage-tile width and shared-memory rows of one element-kernel
+// instantiation.  FP64 runs two CTAs of four warps per SM (two warps per
+// sub-partition, 255 registers each); rows of NL (P + 1) complex FP64 entries
+// beyond about 140 registers spill, so the lowest levels move to shared
+// memory (run_chain's NS), as many as that needs and the SM's 228 KB leave
+// room for: 28,928 bytes per warp ((228 KB - 2 x 1 KB reserved) / 8), with a
+// stage tile narrowed to 32 columns per layer, which is done only where a
+// chunk still holds one degree's 2P + 1 columns.  The FP64 pipe retires one
+// warp FMA in about 64 cycles, so a stencil's two 16-byte shared loads and one
+// store per lane cost nothing measurable; they replace local-memory spills.
+// FP32 keeps every row in registers and 48 columns per layer.
+template <typename T, int P, int KIND, int DENS, int OUTS>
+struct ElemCfg {
+    static constexpr int NL = Chain<KIND, DENS>::NL;
+    static constexpr int NACC = elem_outputs(KIND, OUTS);
+    static constexpr bool TWO_LAYERS = KIND == KIND_TRI && (OUTS & 2) != 0;
+    static constexpr int CH_NARROW = 32;
+    static constexpr int ns_narrow()
+    {
+        if (sizeof(T) == 4) return 0;
+        if ((TWO_LAYERS ? CH_NARROW : 2 * CH_NARROW) < 2 * P + 1) return 0;
+        const size_t per_warp = (228 * 1024 - 2 * 1024) / 8;
+        const size_t base = warp_smem_bytes<double>((P + 1) * (P + 1), NACC, CH_NARROW);
+        const size_t level = (size_t)(P + 1) * 32 * 16;
+        int ns = 0;
+        while (ns < NL - 1 && (NL - ns) * (P + 1) * 4 > 140 && base + (size_t)(ns + 1) * level <= per_warp) ++ns;
+        return ns;
+    }
+    static constexpr int NS = ns_narrow();
+    static constexpr int CH = NS > 0 ? CH_NARROW : KCfg<T>::CHUNK;
+    static constexpr size_t ROW_BYTES = (size_t)NS * (P + 1) * 32 * 16;  // [NS][P + 1][32] double2
+    __host__ __device__ static constexpr size_t warp_bytes(int np_max)
+    {
+        return warp_smem_bytes<T>(np_max, NACC, CH) + ROW_BYTES;  // the first term is a multiple of 128
+    }
+};
 
 // Resident CTAs per SM the element kernel is compiled for, which caps its
 // registers: FP32 chains whose rows leave room run 4 warps per sub-partition
@@ -1285,7 +1408,8 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
 {
     using C = Chain<KIND, DENS>;
     constexpr int NL = C::NL;
-    constexpr int CH = KCfg<T>::CHUNK, LD = KCfg<T>::LD;
+    using Cfg = ElemCfg<T, P, KIND, DENS, OUTS>;
+    constexpr int CH = Cfg::CH, LD = KCfg<T>::LD, NS = Cfg::NS;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -1295,13 +1419,15 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
 
     constexpr bool VEC = (OUTS & 4) != 0;  // vector density: three weighted outputs of one pass
     constexpr int NACC = elem_outputs(KIND, OUTS);
-    unsigned char* wsm = smem_raw + (size_t)wib * warp_smem_bytes<T>(a.np_max, NACC);
+    unsigned char* wsm = smem_raw + (size_t)wib * Cfg::warp_bytes(a.np_max);
+    double2* srows = reinterpret_cast<double2*>(wsm + warp_smem_bytes<T>(a.np_max, NACC, CH));  // NS > 0 only
     T* tile = reinterpret_cast<T*>(wsm);
     T* rowwt = tile + 2 * CH * LD;  // vector density only: [3][32]
     // 2 CH LD sizeof(T) and 96 sizeof(T) are multiples of 16
     LeafSum<T>* accb = reinterpret_cast<LeafSum<T>*>(tile + 2 * CH * LD + (VEC ? 96 : 0));
     long long* rowleaf = reinterpret_cast<long long*>(accb + NACC * a.np_max);
     int* rowinfo = reinterpret_cast<int*>(rowleaf + 32);
+    Walk<sizeof(T) == 8> wk(reinterpret_cast<WarpWalk*>(rowinfo + 32), lane);  // 8-byte aligned
 
     constexpr bool want0 = (OUTS & 1) != 0 || VEC;
     constexpr bool want1 = (KIND == KIND_TRI) && (OUTS & 2) != 0;
@@ -1310,25 +1436,40 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
     const int np = a.np_max;
     const int pw = a.p_max;
 
-    RangeCtx rc;
-    rc.w = w;
-    rc.e_lo = w * a.T;
-    rc.e_hi = min(rc.e_lo + a.T, a.n_elem);
-    // output 1 is the double layer (one hat degree less, scale exponent n + 1),
-    // or a vector component (the single layer's constants)
-    rc.d_out0 = rc.d_out2 = C::D_OUT;
-    rc.d_out1 = VEC ? C::D_OUT : C::D_OUT - 1;
-    rc.shift_n00 = rc.shift_n02 = KIND + 1;
-    rc.shift_n01 = VEC ? KIND + 1 : 1;
-    rc.nacc = NACC;
-
-    int64_t L_last;
-    if (per_elem) {
-        rc.L_first = rc.e_lo;
-        L_last = rc.e_hi - 1;
-    } else {
-        rc.L_first = leaf_search(a.leaf_off, 0, a.n_leaves - 1, rc.e_lo);
-        L_last = leaf_search(a.leaf_off, rc.L_first, a.n_leaves - 1, rc.e_hi - 1);
+    // the range and its constants
+    auto range_ctx = [&]() {
+        RangeCtx rc;
+        rc.w = wk.w();
+        rc.e_lo = wk.e_lo();
+        rc.e_hi = wk.e_hi();
+        rc.L_first = wk.L_first();
+        // output 1 is the double layer (one hat degree less, scale exponent
+        // n + 1), or a vector component (the single layer's constants)
+        rc.d_out0 = rc.d_out2 = C::D_OUT;
+        rc.d_out1 = VEC ? C::D_OUT : C::D_OUT - 1;
+        rc.shift_n00 = rc.shift_n02 = KIND + 1;
+        rc.shift_n01 = VEC ? KIND + 1 : 1;
+        rc.nacc = NACC;
+        return rc;
+    };
+    {
+        const int64_t e_lo = w * a.T, e_hi = min(e_lo + a.T, a.n_elem);
+        int64_t L_first, L_last;
+        if (per_elem) {
+            L_first = e_lo;
+            L_last = e_hi - 1;
+        } else {
+            L_first = leaf_search(a.leaf_off, 0, a.n_leaves - 1, e_lo);
+            L_last = leaf_search(a.leaf_off, L_first, a.n_leaves - 1, e_hi - 1);
+        }
+        wk.set_w(w);
+        wk.set_e_lo(e_lo);
+        wk.set_e_hi(e_hi);
+        wk.set_L_first(L_first);
+        wk.set_L_last(L_last);
+        wk.set_e_cur(e_lo);
+        wk.set_open_leaf(L_first);
+        wk.sync();
     }
 
     for (int k = lane; k < NACC * np; k += 32) accb[k].zero();
@@ -1351,13 +1492,13 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
             }
     };
     if (!per_elem) {
-        zero_leaves(leaf_lower(a.leaf_off, 0, a.n_leaves, rc.e_lo), rc.L_first);
-        if (rc.e_hi == a.n_elem) zero_leaves(L_last + 1, a.n_leaves);
+        zero_leaves(leaf_lower(a.leaf_off, 0, a.n_leaves, wk.e_lo()), wk.L_first());
+        if (wk.e_hi() == a.n_elem) zero_leaves(wk.L_last() + 1, a.n_leaves);
     }
 
     auto leaf_info = [&](int64_t L) -> int {
         bool complete = true;
-        if (!per_elem) complete = __ldg(a.leaf_off + L) >= rc.e_lo && __ldg(a.leaf_off + L + 1) <= rc.e_hi;
+        if (!per_elem) complete = __ldg(a.leaf_off + L) >= wk.e_lo() && __ldg(a.leaf_off + L + 1) <= wk.e_hi();
         const int s = a.leaf_rho ? scale_exponent(__ldg(a.leaf_rho + L)) : 0;
         int pl = pw;
         if (a.leaf_p) {
@@ -1366,22 +1507,26 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
         }
         return s * 128 + (pl + 1) * 2 + (complete ? 1 : 0);
     };
-    long long open_leaf = rc.L_first;
-    int open_info = leaf_info(rc.L_first);
-    __syncwarp();
+    {
+        const int oi = leaf_info(wk.L_first());
+        wk.set_open_info(oi);
+        __syncwarp();
+    }
 
     // Rounds of at most 32 elements.  The next 32 elements of the range are
     // the candidates; candidate b that starts a new leaf is moved to the next
     // multiple of four lanes (the lanes skipped are padding), candidates that
     // no longer fit wait for the next round.  Per-element expansions take 32
     // consecutive elements without padding.
-    int64_t e_cur = rc.e_lo;
 #pragma unroll 1
-    while (e_cur < rc.e_hi) {
+    while (true) {
+        const int64_t e_cur = wk.e_cur(), e_hi = wk.e_hi();
+        if (e_cur >= e_hi) break;
+        const long long open_leaf = wk.open_leaf();
         const int64_t ec = e_cur + lane;
-        const bool cand = ec < rc.e_hi;
+        const bool cand = ec < e_hi;
         int64_t Lc = open_leaf;
-        if (cand) Lc = per_elem ? ec : leaf_search(a.leaf_off, open_leaf, L_last, ec);
+        if (cand) Lc = per_elem ? ec : leaf_search(a.leaf_off, open_leaf, wk.L_last(), ec);
         const long long Lcprev = __shfl_up_sync(0xffffffffu, (long long)Lc, 1);
         const bool cstart = cand && ((lane == 0) ? (Lc != open_leaf) : (Lc != Lcprev));
         const unsigned B = __ballot_sync(0xffffffffu, cstart);
@@ -1446,6 +1591,9 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
         const int last = 31 - __clz(__ballot_sync(0xffffffffu, active));
         rowleaf[lane] = (long long)L;
         rowinfo[lane] = info;
+        wk.set_gstart(gstart);
+        wk.set_n_taken(n_taken);
+        wk.set_last(last);
         if constexpr (VEC) {
             // this lane's element's current components: the row weights (a
             // non-finite component zeroes the whole segment)
@@ -1466,18 +1614,27 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
         load_frame<T, KIND, DENS, VEC>(a.vx, a.vy, a.vz, a.idx, a.sigma, a.n_elem, a.n_vert, e, active, cx, cy, cz,
                                        sexp, errbits, pL, F);
         if (errbits) atomicOr(a.err, errbits);
-        run_chain<T, P, KIND, DENS, VEC ? 1 : OUTS, true>(F, pw, tile, lane, [&](int c0, int ncols) {
+        run_chain<T, P, KIND, DENS, VEC ? 1 : OUTS, true, NS, CH>(F, pw, tile, lane, [&](int c0, int ncols) {
+            const RangeCtx rc = range_ctx();
             if constexpr (VEC)
-                reduce_chunk_vec<T>(a, rc, tile, accb, rowwt, rowleaf, rowinfo, open_leaf, open_info, gstart, c0,
-                                    ncols);
+                reduce_chunk_vec<T>(a, rc, tile, accb, rowwt, rowleaf, rowinfo, wk.open_leaf(), wk.open_info(),
+                                    wk.gstart(), c0, ncols);
             else
-                reduce_chunk<T>(a, rc, tile, accb, rowleaf, rowinfo, open_leaf, open_info, gstart, n_taken, c0,
-                                ncols, want0, want1, per_elem);
-        });
-        // the run open at the end of this round
-        open_leaf = rowleaf[last];
-        open_info = rowinfo[last];
-        e_cur += n_taken;
+                reduce_chunk<T, CH>(a, rc, tile, accb, rowleaf, rowinfo, wk.open_leaf(), wk.open_info(), wk.gstart(),
+                                    wk.n_taken(), c0, ncols, want0, want1, per_elem);
+        }, srows);
+        // the run open at the end of this round (every lane reads the walk
+        // state before it is updated)
+        {
+            const int lst = wk.last();
+            const long long ol = rowleaf[lst];
+            const int oi = rowinfo[lst];
+            const int64_t en = wk.e_cur() + wk.n_taken();
+            wk.sync();
+            wk.set_open_leaf(ol);
+            wk.set_open_info(oi);
+            wk.set_e_cur(en);
+        }
         __syncwarp();
     }
 
@@ -1487,14 +1644,19 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
         if (VEC ? a.coef[ly] == nullptr : ((ly == 0 && !want0) || (ly == 1 && !want1) || ly == 2)) continue;
 #pragma unroll 1
         for (int c = lane; c < np; c += 32)
-            flush_value<T>(a, rc, ly, c, accb[ly * np + c], open_leaf, open_info);
+            flush_value<T>(a, range_ctx(), ly, c, accb[ly * np + c], wk.open_leaf(), wk.open_info());
     }
 }
 
 // Combine the slot partials of leaves that span several warp ranges.  One warp
-// per range boundary w (1 <= w < n_ranges): the leaf L containing element w*T,
-// handled here iff w is the last range L touches.  The FP64 partials are summed
-// in range order (compensated), then scaled like a complete run.
+// per range boundary w (1 <= w < n_ranges) and block of 32 columns
+// (blockIdx.y): the leaf L containing element w*T is handled there iff w is
+// the last range L touches.  A lane sums its column's FP64 partials of the
+// ranges wf..w (partial i of the leaf into accumulator i mod 4, each a
+// compensated Neumaier sum, the four combined in a fixed order: the result
+// does not depend on scheduling), then scales the total like a complete run.
+// The four chains and the column blocks keep the dependent FP64 adds short
+// when a small problem's leaf spans tens of ranges.
 static __global__ void q2x_fixup_kernel(const ElemArgs a, int d0, int d1, int d2, int s0, int s1, int s2)
 {
     const int lane = threadIdx.x & 31;
@@ -1506,6 +1668,9 @@ static __global__ void q2x_fixup_kernel(const ElemArgs a, int d0, int d1, int d2
     if (o0 < 0 || o1 > a.n_elem || o1 <= o0) return;  // bad offsets (reported elsewhere)
     if (o0 >= e) return;                 // starts in this range: not spanning here
     if ((o1 - 1) / a.T != w) return;     // not the last range of L
+    const int np = a.np_max;
+    const int c = (int)blockIdx.y * 32 + lane;
+    if (c >= np) return;
     const int64_t wf = o0 / a.T;
     const int slot_first = (o0 == wf * a.T) ? 0 : 1;
     const int s = a.leaf_rho ? scale_exponent(__ldg(a.leaf_rho + L)) : 0;
@@ -1514,36 +1679,57 @@ static __global__ void q2x_fixup_kernel(const ElemArgs a, int d0, int d1, int d2
         pl = __ldg(a.leaf_p + L);
         if (pl < 0 || pl > a.p_max) pl = -1;
     }
-    const int np = a.np_max;
+    const int desc = col_desc(c);
     const double* slots = a.slots;
     for (int ly = 0; ly < a.nacc; ++ly) {
         if (a.coef[ly] == nullptr) continue;
-        for (int c = lane; c < np; c += 32) {
-            double sum = slots[((wf * 2 + slot_first) * a.nacc + ly) * (int64_t)np + c];
-            double comp = 0.0;
-            for (int64_t ww = wf + 1; ww <= w; ++ww) {
-                const double x = slots[((ww * 2 + 0) * a.nacc + ly) * (int64_t)np + c];
-                // Kahan-Babuska (Neumaier) step
-                const double t = sum + x;
-                if (fabs(sum) >= fabs(x))
-                    comp += (sum - t) + x;
-                else
-                    comp += (x - t) + sum;
-                sum = t;
-            }
-            sum += comp;
-            const int desc = col_desc(c);
-            const double v = ((desc & 31) <= pl)
-                                 ? finish_desc(sum, a.norm, desc, ly == 0 ? d0 : ly == 1 ? d1 : d2,
-                                               ly == 0 ? s0 : ly == 1 ? s1 : s2, s)
-                                 : 0.0;
-            double* dst = a.coef[ly] + L * np + c;
-            if (a.accumulate)
-                *dst += v;
+        // partial i: range wf + i (slot slot_first for i = 0, else slot 0)
+        auto partial = [&](int64_t i) {
+            const int64_t row = (i == 0) ? wf * 2 + slot_first : (wf + i) * 2;
+            return __ldg(slots + (row * a.nacc + ly) * (int64_t)np + c);
+        };
+        double sum[4] = {0.0, 0.0, 0.0, 0.0}, comp[4] = {0.0, 0.0, 0.0, 0.0};
+        auto step = [](double& sm, double& cp, double x) {  // Neumaier
+            const double t = sm + x;
+            if (fabs(sm) >= fabs(x))
+                cp += (sm - t) + x;
             else
-                *dst = v;
+                cp += (x - t) + sm;
+            sm = t;
+        };
+        const int64_t K = w - wf + 1;  // partials of the leaf
+        int64_t i = 0;
+        for (; i + 4 <= K; i += 4) {
+            double x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = partial(i + u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) step(sum[u], comp[u], x[u]);
         }
+        for (int u = 0; i < K; ++i, ++u) step(sum[u], comp[u], partial(i));
+        double tot = sum[0], tc = comp[0] + comp[1] + comp[2] + comp[3];
+        for (int u = 1; u < 4; ++u) step(tot, tc, sum[u]);
+        tot += tc;
+        const double v = ((desc & 31) <= pl)
+                             ? finish_desc(tot, a.norm, desc, ly == 0 ? d0 : ly == 1 ? d1 : d2,
+                                           ly == 0 ? s0 : ly == 1 ? s1 : s2, s)
+                             : 0.0;
+        double* dst = a.coef[ly] + L * np + c;
+        if (a.accumulate)
+            *dst += v;
+        else
+            *dst = v;
     }
+}
+
+// The fix-up launch for a range split (n_ranges > 1): 4 warps per block over
+// the boundaries, one block row per 32 columns.
+inline cudaError_t launch_fixup(const ElemArgs& a, cudaStream_t st, int d0, int d1, int d2, int s0, int s1, int s2)
+{
+    if (a.n_ranges <= 1) return cudaSuccess;
+    const dim3 grid((unsigned)((a.n_ranges - 1 + 3) / 4), (unsigned)((a.np_max + 31) / 32));
+    q2x_fixup_kernel<<<grid, 128, 0, st>>>(a, d0, d1, d2, s0, s1, s2);
+    return cudaGetLastError();
 }
 
 }  // namespace q2x
@@ -1557,6 +1743,13 @@ namespace q2x {
 // plan's p_max <= P needs no more (warp_smem_bytes grows with the column count).
 constexpr int kMaxDevices = 64;
 
+// dynamic shared memory of one launch: every warp's region
+template <typename T, int P, int KIND, int DENS, int OUTS>
+size_t elem_launch_smem(int np_max)
+{
+    return elem_warps_per_cta<T>() * ElemCfg<T, P, KIND, DENS, OUTS>::warp_bytes(np_max);
+}
+
 template <typename T, int P, int KIND, int DENS, int OUTS>
 cudaError_t elem_smem_attribute()
 {
@@ -1565,7 +1758,7 @@ cudaError_t elem_smem_attribute()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < kMaxDevices && done[dev]) return cudaSuccess;
-    const size_t smem_max = elem_warps_per_cta<T>() * warp_smem_bytes<T>((P + 1) * (P + 1), elem_outputs(KIND, OUTS));
+    const size_t smem_max = elem_launch_smem<T, P, KIND, DENS, OUTS>((P + 1) * (P + 1));
     e = cudaFuncSetAttribute(q2x_elem_kernel<T, P, KIND, DENS, OUTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_max);
     if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) done[dev] = 1;
@@ -1573,19 +1766,21 @@ cudaError_t elem_smem_attribute()
 }
 
 template <typename T, int P, int KIND, int DENS, int OUTS>
-cudaError_t launch_elem(const ElemArgs& a, int grid, size_t smem, cudaStream_t st)
+cudaError_t launch_elem(const ElemArgs& a, int grid, cudaStream_t st)
 {
     cudaError_t e = elem_smem_attribute<T, P, KIND, DENS, OUTS>();
     if (e != cudaSuccess) return e;
+    const size_t smem = elem_launch_smem<T, P, KIND, DENS, OUTS>(a.np_max);
     q2x_elem_kernel<T, P, KIND, DENS, OUTS><<<grid, elem_warps_per_cta<T>() * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T, int P, int KIND, int DENS, int OUTS>
-cudaError_t occupancy_elem(int* blocks_per_sm, size_t smem)
+cudaError_t occupancy_elem(int* blocks_per_sm, int np_max)
 {
     cudaError_t e = elem_smem_attribute<T, P, KIND, DENS, OUTS>();
     if (e != cudaSuccess) return e;
+    const size_t smem = elem_launch_smem<T, P, KIND, DENS, OUTS>(np_max);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, q2x_elem_kernel<T, P, KIND, DENS, OUTS>,
                                                          elem_warps_per_cta<T>() * 32, smem);
 }
@@ -1593,14 +1788,15 @@ cudaError_t occupancy_elem(int* blocks_per_sm, size_t smem)
 }  // namespace q2x
 
 #define Q2X_INSTANTIATE(T, P, KIND, DENS, OUTS)                                                  \
-    template cudaError_t q2x::launch_elem<T, P, KIND, DENS, OUTS>(const q2x::ElemArgs&, int, size_t, \
-                                                                  cudaStream_t);                   \
-    template cudaError_t q2x::occupancy_elem<T, P, KIND, DENS, OUTS>(int*, size_t);
+    template cudaError_t q2x::launch_elem<T, P, KIND, DENS, OUTS>(const q2x::ElemArgs&, int, cudaStream_t); \
+    template cudaError_t q2x::occupancy_elem<T, P, KIND, DENS, OUTS>(int*, int);                    \
+    template size_t q2x::elem_launch_smem<T, P, KIND, DENS, OUTS>(int);
 
 #define Q2X_DECLARE(T, P, KIND, DENS, OUTS)                                                      \
     extern template cudaError_t q2x::launch_elem<T, P, KIND, DENS, OUTS>(const q2x::ElemArgs&, int, \
-                                                                         size_t, cudaStream_t);    \
-    extern template cudaError_t q2x::occupancy_elem<T, P, KIND, DENS, OUTS>(int*, size_t);
+                                                                         cudaStream_t);            \
+    extern template cudaError_t q2x::occupancy_elem<T, P, KIND, DENS, OUTS>(int*, int);             \
+    extern template size_t q2x::elem_launch_smem<T, P, KIND, DENS, OUTS>(int);
 
 // capacity bins of the kernels
 #define Q2X_FOR_BINS(X, T, KIND, DENS, OUTS)                                                     \

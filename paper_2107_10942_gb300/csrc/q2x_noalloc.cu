@@ -53,7 +53,7 @@ std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
 unsigned* g_err_ptr[kMaxDevices] = {};
 
-using LaunchFn = cudaError_t (*)(const q2x::ElemArgs&, int, size_t, cudaStream_t);
+using LaunchFn = cudaError_t (*)(const q2x::ElemArgs&, int, cudaStream_t);
 #define Q2X_NA_ENTRY(T, P, KIND, DENS, OUTS) &q2x::launch_elem<T, P, KIND, DENS, OUTS>,
 #define Q2X_NA_ROW(T, DENS, OUTS) {Q2X_FOR_BINS(Q2X_NA_ENTRY, T, q2x::KIND_TRI, DENS, OUTS)},
 #define Q2X_NA_DENS(T, DENS) {Q2X_NA_ROW(T, DENS, 1) Q2X_NA_ROW(T, DENS, 2) Q2X_NA_ROW(T, DENS, 3)},
@@ -182,16 +182,12 @@ extern "C" q2x_status q2x_triangles_noalloc(int p_max, q2x_norm norm, q2x_precis
     a.err = err;
 
     const int wpc = prec ? q2x::elem_warps_per_cta<float>() : q2x::elem_warps_per_cta<double>();
-    const size_t smem =
-        wpc * (prec ? q2x::warp_smem_bytes<float>(np, a.nacc) : q2x::warp_smem_bytes<double>(np, a.nacc));
     const int grid = (int)((n_ranges + wpc - 1) / wpc);
     const int outs = (coef_single ? 1 : 0) | (coef_double ? 2 : 0);
-    if (kTri[prec][density][outs - 1][bin](a, grid, smem, stream) != cudaSuccess) return Q2X_ERR_CUDA;
+    if (kTri[prec][density][outs - 1][bin](a, grid, stream) != cudaSuccess) return Q2X_ERR_CUDA;
     if (n_ranges > 1) {
         const int d_out = (density == Q2X_DENSITY_LINEAR) ? 3 : 2;
-        const int fgrid = (int)((n_ranges - 1 + 3) / 4);
-        q2x::q2x_fixup_kernel<<<fgrid, 128, 0, stream>>>(a, d_out, d_out - 1, d_out, 2, 1, 2);
-        if (cudaGetLastError() != cudaSuccess) return Q2X_ERR_CUDA;
+        if (q2x::launch_fixup(a, stream, d_out, d_out - 1, d_out, 2, 1, 2) != cudaSuccess) return Q2X_ERR_CUDA;
     }
     return Q2X_OK;
 }

@@ -87,6 +87,27 @@ def test_parity(q2x, orc, kind, density, layer, both, prec, p):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind,density,layer,both", [("segment", "const", 0, False),
+                                                     ("triangle", "const", 0, True),
+                                                     ("tetra", "const", 0, False)])
+def test_runs_of_tiny_and_empty_leaves(q2x, orc, kind, density, layer, both, prec):
+    # more than 32 leaves start inside one 32-element round (single-element
+    # and empty leaves): the kernel's leaf lookup must leave its 32-leaf
+    # window for the search in leaf_off; the rest fit the window
+    sizes = [1] * 45 + [0] * 20 + [2, 0] * 25 + [1, 0, 0, 3] * 12 + [70, 0, 0, 0, 1] + [1] * 33
+    p = 6
+    prob = random_problem(kind, sizes, seed=29, p=p, density=density)
+    cs, cd = run(q2x, prob, prec, single=True, double=both)
+    assert norm_err(cs, oracle_coef(orc, prob, layer=0), p, prob["leaf_rho"], 0) <= TOL[prec]
+    if cd is not None:
+        assert norm_err(cd, oracle_coef(orc, prob, layer=1), p, prob["leaf_rho"], 1) <= TOL[prec]
+    empty = np.where(np.diff(prob["leaf_off"]) == 0)[0]
+    for c in (cs, cd):
+        if c is not None:
+            assert np.all(c[empty] == 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_moment_norm(q2x, orc, prec):
     for kind, density in (("segment", "const"), ("triangle", "linear"), ("tetra", "const")):
         prob = random_problem(kind, SIZES, seed=5, p=9, density=density)
