@@ -60,13 +60,13 @@ DEFAULT_WORKLOAD = "sphere-L9-const"
 # executed flops of the element kernels, from one ncu capture of the current
 # kernel on each workload (None: not captured since the kernel last changed).
 # Executed flops: FP64 2 x DFMA + DADD + DMUL thread instructions; FP32
-# 4 x FFMA2 + 2 x FFMA + 2 x FADD2 + FADD + FMUL (per-opcode thread counts:
+# 4 x FFMA2 + 2 x FFMA + 2 x FADD2 + 2 x FMUL2 + FADD + FMUL (per-opcode thread counts:
 # the packed instructions are not in the FFMA/FADD class counters).
 KERNEL_COUNTERS = {
-    ("sphere-L9-const", "fp64"): {},
-    ("sphere-L9-const", "fp32"): {},
-    ("sphere-L7-linear", "fp64"): {},
-    ("sphere-L7-linear", "fp32"): {},
+    ("sphere-L9-const", "fp64"): dict(traffic=218551296 + 112463104, executed_flops=35642946312),
+    ("sphere-L9-const", "fp32"): dict(traffic=222372096 + 112917504, executed_flops=41174190806),
+    ("sphere-L7-linear", "fp64"): dict(traffic=9513984 + 1454848, executed_flops=2863254784),
+    ("sphere-L7-linear", "fp32"): dict(traffic=9380608 + 1536, executed_flops=3403618476),
 }
 COUNTER_SOURCE = "ncu --set full capture of one launch of this kernel on this workload"
 
@@ -482,28 +482,63 @@ def main():
     keys = ("vxyz", "idx", "sigma", "leaf_off", "leaf_c", "leaf_rho")
     host = {k: torch.from_numpy(np.ascontiguousarray(prob[k])).pin_memory() for k in keys}
     h2d = sum(t.numel() * t.element_size() for t in host.values())
-    out_h = [torch.empty((n_leaves, nc), dtype=torch.float64).pin_memory() for _ in layers]
-    d2h = sum(o.numel() * 8 for o in out_h)
-    plan = q.Plan(P, precision="fp64")
+    # A streaming pipeline, as a serving loop runs it: step k's host-to-device
+    # copy, compute and device-to-host copy go on three streams, with the
+    # device inputs and outputs double-buffered, so that the copies of steps
+    # k + 1 and k - 1 overlap the compute of step k.  Every step still copies
+    # its inputs in and its coefficients out inside the timed region.
+    out_h = [[torch.empty((n_leaves, nc), dtype=torch.float64).pin_memory() for _ in layers] for _ in range(2)]
+    d2h = sum(o.numel() * 8 for o in out_h[0])
+    s_h2d, s_cmp, s_d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    plan = q.Plan(P, precision="fp64", stream=s_cmp)
+    dbuf = [{k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()} for _ in range(2)]
+    obuf = [[torch.empty((n_leaves, nc), dtype=torch.float64, device=dev) for _ in layers] for _ in range(2)]
+    ev_in = [torch.cuda.Event() for _ in range(2)]    # inputs of buffer b copied
+    ev_cmp = [torch.cuda.Event() for _ in range(2)]   # compute on buffer b done
+    ev_out = [torch.cuda.Event() for _ in range(2)]   # outputs of buffer b copied out
+    used = [False, False]
 
-    def e2e_step():
-        g = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+    def e2e_step(k):
+        b = k & 1
+        if used[b]:
+            s_h2d.wait_event(ev_cmp[b])  # step k - 2 has read these inputs
+        with torch.cuda.stream(s_h2d):
+            for key, v in host.items():
+                dbuf[b][key].copy_(v, non_blocking=True)
+            ev_in[b].record(s_h2d)
+        s_cmp.wait_event(ev_in[b])
+        if used[b]:
+            s_cmp.wait_event(ev_out[b])  # step k - 2's outputs have been copied out
+        g = dbuf[b]
+        outs = {"coef_single": obuf[b][0]} if single else {}
+        if double:
+            outs["coef_double"] = obuf[b][1 if single else 0]
         cs, cd = plan.triangles(g["vxyz"], g["idx"], g["sigma"], g["leaf_off"], g["leaf_c"], g["leaf_rho"], None,
-                                density=wl["density"], single=single, double=double)
-        for o, c in zip(out_h, [c for c in (cs, cd) if c is not None]):
-            o.copy_(c, non_blocking=True)
+                                density=wl["density"], single=single, double=double, **outs)
+        ev_cmp[b].record(s_cmp)
+        s_d2h.wait_event(ev_cmp[b])
+        with torch.cuda.stream(s_d2h):
+            for o, c in zip(out_h[b], [c for c in (cs, cd) if c is not None]):
+                o.copy_(c, non_blocking=True)
+            ev_out[b].record(s_d2h)
+        used[b] = True
 
-    for _ in range(args.warmup):
-        e2e_step()
+    for k in range(args.warmup):
+        e2e_step(k)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.time()
-    e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
+    e0.record(s_cmp)
+    s_h2d.wait_event(e0)
+    s_d2h.wait_event(e0)
+    for k in range(args.steps):
+        e2e_step(args.warmup + k)
+    for b in range(2):
+        if used[b]:
+            s_cmp.wait_event(ev_out[b])
+    e1.record(s_cmp)
     torch.cuda.synchronize()
     t1 = time.time()
     if clk:
@@ -639,7 +674,10 @@ def main():
         "errors_vs_oracle": errs or None,
         "cpu_baseline": cpu,
         "e2e": {"value": total_moments / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "pipeline": "each step copies its inputs from pinned host memory and its coefficients back; "
+                            "the copies of neighbouring steps overlap this step's compute (three streams, "
+                            "double-buffered device inputs and outputs)"},
         "gpu_launches": r64["launches"],
         "clocks": clocks,
     }

@@ -226,15 +226,15 @@ q2x_status q2x_triangles_single_vjp(q2x_plan_t plan, int64_t n_elem, int64_t n_v
                                     const int32_t* leaf_p, const double* grad_coef,
                                     double* grad_vxyz, double* grad_sigma);
 
-/* ---- Ragged mixed batch in one persistent launch (CUDA graph) ----------
+/* ---- Ragged mixed batch in one CUDA-graph replay -----------------------
  * Several element kinds (segments, triangles, tetrahedra) share one leaf set;
  * every leaf has its own degree p_leaf <= p_max and its own element counts.
  * q2x_batch_build (a set-up call: it copies leaf_p and the leaf offsets to the
  * host, allocates the batch's device memory and synchronises) cuts the work
  * into tiles of at most tile_elems elements of one kind inside one leaf,
- * orders them (grouped by kind and degree, most expensive first) and captures
- * [counter reset, one persistent kernel over all tiles, per-leaf combine] in a
- * CUDA graph.  q2x_batch_run replays that graph on the plan's stream: coef
+ * orders them (by degree bin, kind and cost, most expensive first) and captures
+ * [counter reset, one persistent kernel per (kind, degree bin) group of tiles,
+ * per-leaf combine] in a CUDA graph.  q2x_batch_run replays that graph on the plan's stream: coef
  * (n_leaves x (p_max+1)^2) receives, per leaf, the sum of the single-layer
  * coefficients of all its elements of all kinds (zero above p_leaf), added in
  * a fixed order.  The descriptor's device arrays must stay valid and

@@ -1,15 +1,19 @@
-// q2x_batch.cuh -- ragged mixed-kind Q2X batch: one persistent kernel over a
+// q2x_batch.cuh -- ragged mixed-kind Q2X batch: persistent kernels over a
 // tile list, then a deterministic per-leaf combine.
 //
 // A tile is a run of at most T elements of ONE kind inside ONE leaf, so every
 // round of 32 elements a warp processes shares the leaf centre, scale and
 // degree p_leaf: the degree loop runs exactly to p_leaf (no work above it),
 // every staged chunk is summed by the pairwise fast path, and each tile ends
-// with one finished FP64 row of partial coefficients.  Warps of a persistent
-// grid pull tiles through an atomic counter in the host-chosen order (grouped
-// by kind and degree bin, most expensive first).  The combine kernel adds the
-// partial rows of each leaf in slot order (slots are numbered leaf by leaf),
-// so the result does not depend on which warp ran which tile.
+// with one finished FP64 row of partial coefficients.  The host orders the
+// tiles by degree bin (highest first), kind and cost, and cuts the list into
+// groups of one (kind, bin); each group has its own persistent kernel,
+// compiled for its chain alone (registers, and so resident warps, follow that
+// chain, not the most expensive one), whose warps pull the group's tiles
+// through the group's atomic counter.  The groups' kernels run on parallel
+// graph branches, so one group's tail overlaps the next.  The combine kernel
+// adds the partial rows of each leaf in slot order (slots are numbered leaf by
+// leaf), so the result does not depend on which warp ran which tile.
 #pragma once
 
 #include "q2x_kernels.cuh"
@@ -45,23 +49,34 @@ struct BatchArgs {
     int p_max, np_max, norm;
     const BatchTile* tiles;
     int64_t n_tiles;
-    unsigned long long* counter;
+    unsigned long long* counter;  // one per group
     double* partial;  // [n_slots][np_max]
     unsigned* err;
 };
 
 constexpr int BATCH_WARPS = 4;
 
-// stage tile [2 CHUNK][LD] of T (single-layer passes stage twice CHUNK
-// columns per reduction), then the tile's column sums [np_max] (LeafSum)
+// stage tile [2 CH][LD] of T (single-layer passes stage 2 CH columns per
+// reduction), then the tile's column sums [np] (LeafSum)
 template <typename T>
-__host__ __device__ constexpr size_t batch_warp_smem_bytes(int np_max)
+__host__ __device__ constexpr size_t batch_warp_smem_bytes(int np, int ch = KCfg<T>::CHUNK)
 {
-    return (sizeof(T) * (size_t)(2 * KCfg<T>::CHUNK * KCfg<T>::LD) + sizeof(LeafSum<T>) * (size_t)np_max + 127) /
-           128 * 128;
+    return (sizeof(T) * (size_t)(2 * ch * KCfg<T>::LD) + sizeof(LeafSum<T>) * (size_t)np + 127) / 128 * 128;
 }
 
+// One group's kernel: the chain's capacity P, its stage-tile width and the
+// CTAs per SM it is compiled for.  FP32 uses the element kernel's register
+// targets (CTAs of four warps here: 4, 3 or 2 per SM) and 40-column chunks, so
+// that 16 warps of the small chains fit in shared memory.
 template <typename T, int P, int KIND, int DENS>
+struct BatchCfg {
+    static constexpr int CH = sizeof(T) == 4 ? 40 : KCfg<T>::CHUNK;
+    static constexpr int NP = (P + 1) * (P + 1);
+    static constexpr int MIN_CTAS = sizeof(T) == 4 ? min_ctas<T, P, KIND, DENS, 1>() / 4 : 2;
+    static constexpr size_t WARP_BYTES = batch_warp_smem_bytes<T>(NP, CH);
+};
+
+template <typename T, int P, int KIND, int DENS, int CH>
 __device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& t, T* tile, LeafSum<T>* accb,
                                            int lane)
 {
@@ -80,7 +95,8 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& 
                  cz = __ldg(b.leaf_c + 2 * b.n_leaves + L);
     if (!(finite_bits(cx) && finite_bits(cy) && finite_bits(cz))) errbits |= 2u;
     const int sexp = b.leaf_rho ? scale_exponent(__ldg(b.leaf_rho + L)) : 0;
-    for (int c = lane; c < np; c += 32) accb[c].zero();
+    constexpr int NPC = (P + 1) * (P + 1);  // accb holds the columns up to the capacity
+    for (int c = lane; c < NPC; c += 32) accb[c].zero();
     __syncwarp();
     if (pL >= 0) {
 #pragma unroll 1
@@ -91,7 +107,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& 
             Frame<T, C::NL> F;
             load_frame<T, KIND, DENS>(K.vx, K.vy, K.vz, K.idx, K.sigma, K.n_elem, K.n_vert, e, active, cx, cy,
                                       cz, sexp, errbits, pl, F);
-            run_chain<T, P, KIND, DENS, 1, true>(F, pL, tile, lane, [&](int c0, int ncols) {
+            run_chain<T, P, KIND, DENS, 1, true, 0, CH>(F, pL, tile, lane, [&](int c0, int ncols) {
                 // each round's 32 rows summed pairwise, the rounds accumulated
                 // in a LeafSum (compensated in FP32)
                 for (int j = lane; j < ncols; j += 32) accb[c0 + j].add(sum_rows32(tile + j * LD));
@@ -111,43 +127,71 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& 
     __syncwarp();
 }
 
-#define Q2X_BATCH_CASE(T, COMBO, KIND, DENS, BIN, P)                                              \
-    case (COMBO)*5 + (BIN):                                                                       \
-        batch_tile<T, P, KIND, DENS>(b, t, tile, accb, lane);                                     \
-        break;
-#define Q2X_BATCH_COMBO(T, COMBO, KIND, DENS)                                                     \
-    Q2X_BATCH_CASE(T, COMBO, KIND, DENS, 0, 4)                                                    \
-    Q2X_BATCH_CASE(T, COMBO, KIND, DENS, 1, 8)                                                    \
-    Q2X_BATCH_CASE(T, COMBO, KIND, DENS, 2, 12)                                                   \
-    Q2X_BATCH_CASE(T, COMBO, KIND, DENS, 3, 16)                                                   \
-    Q2X_BATCH_CASE(T, COMBO, KIND, DENS, 4, 20)
-
-template <typename T>
-__global__ void __launch_bounds__(BATCH_WARPS * 32, 2) q2x_batch_kernel(const BatchArgs b)
+// The persistent kernel of one group: tiles t0 .. t1-1 of the sorted list,
+// pulled through the group's counter g.
+template <typename T, int P, int KIND, int DENS>
+__global__ void __launch_bounds__(BATCH_WARPS * 32, (BatchCfg<T, P, KIND, DENS>::MIN_CTAS))
+    q2x_batch_group_kernel(const BatchArgs b, int64_t t0, int64_t t1, int g)
 {
+    using BC = BatchCfg<T, P, KIND, DENS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    unsigned char* wsm = smem_raw + (size_t)wib * batch_warp_smem_bytes<T>(b.np_max);
+    unsigned char* wsm = smem_raw + (size_t)wib * BC::WARP_BYTES;
     T* tile = reinterpret_cast<T*>(wsm);
-    LeafSum<T>* accb = reinterpret_cast<LeafSum<T>*>(tile + 2 * KCfg<T>::CHUNK * KCfg<T>::LD);  // 2 CHUNK LD sizeof(T) % 8 == 0
+    LeafSum<T>* accb = reinterpret_cast<LeafSum<T>*>(tile + 2 * BC::CH * KCfg<T>::LD);  // 2 CH LD sizeof(T) % 8 == 0
 #pragma unroll 1
     while (true) {
         unsigned long long ti = 0;
-        if (lane == 0) ti = atomicAdd(b.counter, 1ull);
+        if (lane == 0) ti = atomicAdd(b.counter + g, 1ull);
         ti = __shfl_sync(0xffffffffu, ti, 0);
-        if (ti >= (unsigned long long)b.n_tiles) break;
-        const BatchTile t = b.tiles[ti];
-        switch (t.combo * 5 + t.bin) {
-            Q2X_BATCH_COMBO(T, 0, KIND_SEG, DENS_CONST)
-            Q2X_BATCH_COMBO(T, 1, KIND_TRI, DENS_CONST)
-            Q2X_BATCH_COMBO(T, 2, KIND_TRI, DENS_LINEAR)
-            Q2X_BATCH_COMBO(T, 3, KIND_TET, DENS_CONST)
-            default:
-                break;
-        }
+        if (ti >= (unsigned long long)(t1 - t0)) break;
+        const BatchTile t = b.tiles[t0 + (int64_t)ti];
+        batch_tile<T, P, KIND, DENS, BC::CH>(b, t, tile, accb, lane);
     }
 }
+
+// Host entry points of one group's kernel (explicitly instantiated in
+// q2x_batch_f32.cu / q2x_batch_f64.cu).
+struct BatchGroupFns {
+    cudaError_t (*launch)(const BatchArgs&, int64_t t0, int64_t t1, int g, int grid, cudaStream_t);
+    cudaError_t (*occupancy)(int* blocks_per_sm);
+    size_t smem;
+};
+
+template <typename T, int P, int KIND, int DENS>
+cudaError_t batch_group_occupancy(int* blocks_per_sm)
+{
+    const size_t smem = BATCH_WARPS * BatchCfg<T, P, KIND, DENS>::WARP_BYTES;
+    cudaError_t e = cudaFuncSetAttribute(q2x_batch_group_kernel<T, P, KIND, DENS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, q2x_batch_group_kernel<T, P, KIND, DENS>,
+                                                         BATCH_WARPS * 32, smem);
+}
+
+template <typename T, int P, int KIND, int DENS>
+cudaError_t batch_group_launch(const BatchArgs& b, int64_t t0, int64_t t1, int g, int grid, cudaStream_t st)
+{
+    const size_t smem = BATCH_WARPS * BatchCfg<T, P, KIND, DENS>::WARP_BYTES;
+    cudaError_t e = cudaFuncSetAttribute(q2x_batch_group_kernel<T, P, KIND, DENS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    q2x_batch_group_kernel<T, P, KIND, DENS><<<grid, BATCH_WARPS * 32, smem, st>>>(b, t0, t1, g);
+    return cudaGetLastError();
+}
+
+#define Q2X_BATCH_FNS(T, KIND, DENS, P)                                                            \
+    BatchGroupFns{&batch_group_launch<T, P, KIND, DENS>, &batch_group_occupancy<T, P, KIND, DENS>,    \
+                  BATCH_WARPS * BatchCfg<T, P, KIND, DENS>::WARP_BYTES}
+#define Q2X_BATCH_FNS_ROW(T, KIND, DENS)                                                           \
+    {Q2X_BATCH_FNS(T, KIND, DENS, 4), Q2X_BATCH_FNS(T, KIND, DENS, 8), Q2X_BATCH_FNS(T, KIND, DENS, 12), \
+     Q2X_BATCH_FNS(T, KIND, DENS, 16), Q2X_BATCH_FNS(T, KIND, DENS, 20)}
+
+// [combo][bin] of a precision: combo 0 segments, 1 triangles constant
+// density, 2 triangles linear density, 3 tetrahedra; bins P = 4, 8, 12, 16, 20
+const BatchGroupFns* batch_group_table_f32();
+const BatchGroupFns* batch_group_table_f64();
 
 // coef[L] (+)= sum of the partial rows slot_off[L] .. slot_off[L+1]-1, in order
 __global__ void q2x_batch_combine(const double* __restrict__ partial, const int64_t* __restrict__ slot_off,

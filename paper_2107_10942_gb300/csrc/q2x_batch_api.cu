@@ -1,5 +1,6 @@
-// q2x_batch_api.cu -- ragged mixed batch (include/q2x.h): tile list, graph
-// capture of the persistent kernel and the per-leaf combine, autotuner.
+// q2x_batch_api.cu -- ragged mixed batch (include/q2x.h): tile list and its
+// groups, graph capture of the groups' persistent kernels and the per-leaf
+// combine, autotuner.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -11,10 +12,6 @@
 #include "q2x_plan.h"
 
 namespace q2x {
-cudaError_t batch_launch_f32(const BatchArgs& b, int grid, size_t smem, cudaStream_t st);
-cudaError_t batch_occupancy_f32(int* blocks_per_sm, size_t smem);
-cudaError_t batch_launch_f64(const BatchArgs& b, int grid, size_t smem, cudaStream_t st);
-cudaError_t batch_occupancy_f64(int* blocks_per_sm, size_t smem);
 
 __global__ void q2x_batch_combine(const double* __restrict__ partial, const int64_t* __restrict__ slot_off,
                                   int np, int64_t n_leaves, double* coef, int accumulate)
@@ -40,12 +37,11 @@ struct q2x_batch_s {
     q2x::BatchTile* d_tiles = nullptr;
     int64_t* d_slot_off = nullptr;
     double* d_partial = nullptr;
-    unsigned long long* d_counter = nullptr;
+    unsigned long long* d_counter = nullptr;  // one per group
     int64_t n_tiles = 0, n_slots = 0, n_leaves = 0;
     double* coef = nullptr;
     int accumulate = 0;
-    int grid = 0;
-    size_t smem = 0;
+    int n_groups = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -152,6 +148,19 @@ q2x_status build_batch(q2x_plan_t plan, const q2x_batch_desc* d, int tile_elems,
     });
     std::vector<q2x::BatchTile> sorted(tiles.size());
     for (size_t i = 0; i < ord.size(); ++i) sorted[i] = tiles[ord[i]];
+    // groups: runs of one (kind, bin) in that order, one persistent kernel each
+    struct Group {
+        int combo, bin;
+        int64_t t0, t1;
+        int grid;
+    };
+    std::vector<Group> groups;
+    for (int64_t i = 0; i < (int64_t)sorted.size(); ++i) {
+        if (groups.empty() || groups.back().combo != sorted[i].combo || groups.back().bin != sorted[i].bin)
+            groups.push_back(Group{sorted[i].combo, sorted[i].bin, i, i + 1, 0});
+        else
+            groups.back().t1 = i + 1;
+    }
 
     q2x_batch_s* b = new q2x_batch_s();
     b->plan = plan;
@@ -167,7 +176,8 @@ q2x_status build_batch(q2x_plan_t plan, const q2x_batch_desc* d, int tile_elems,
     ok = ok && cudaMalloc(&b->d_tiles, sizeof(q2x::BatchTile) * std::max<int64_t>(1, b->n_tiles)) == cudaSuccess;
     ok = ok && cudaMalloc(&b->d_slot_off, sizeof(int64_t) * (nl + 1)) == cudaSuccess;
     ok = ok && cudaMalloc(&b->d_partial, sizeof(double) * std::max<int64_t>(1, slot) * np) == cudaSuccess;
-    ok = ok && cudaMalloc(&b->d_counter, sizeof(unsigned long long)) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_counter, sizeof(unsigned long long) * std::max<size_t>(1, groups.size())) ==
+                   cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_batch(b);
@@ -204,23 +214,44 @@ q2x_status build_batch(q2x_plan_t plan, const q2x_batch_desc* d, int tile_elems,
     a.counter = b->d_counter;
     a.partial = b->d_partial;
     a.err = plan->d_err;
-    b->smem = q2x::BATCH_WARPS * (b->prec ? q2x::batch_warp_smem_bytes<float>(np) : q2x::batch_warp_smem_bytes<double>(np));
-    int occ = 0;
-    e = b->prec ? q2x::batch_occupancy_f32(&occ, b->smem) : q2x::batch_occupancy_f64(&occ, b->smem);
-    if (e != cudaSuccess || occ <= 0) {
-        free_batch(b);
-        return q2x_fail(plan, Q2X_ERR_CUDA, "batch: kernel does not fit (%s)", cudaGetErrorString(e));
+    const q2x::BatchGroupFns* fns = b->prec ? q2x::batch_group_table_f32() : q2x::batch_group_table_f64();
+    for (Group& gr : groups) {
+        const q2x::BatchGroupFns& f = fns[gr.combo * 5 + gr.bin];
+        int occ = 0;
+        e = f.occupancy(&occ);
+        if (e != cudaSuccess || occ <= 0) {
+            free_batch(b);
+            return q2x_fail(plan, Q2X_ERR_CUDA, "batch: group kernel does not fit (smem %zu, %s)", f.smem,
+                            cudaGetErrorString(e));
+        }
+        const int64_t want = (gr.t1 - gr.t0 + q2x::BATCH_WARPS - 1) / q2x::BATCH_WARPS;
+        gr.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * plan->num_sms, want));
     }
-    const int64_t want = (b->n_tiles + q2x::BATCH_WARPS - 1) / q2x::BATCH_WARPS;
-    b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * plan->num_sms, want));
+    b->n_groups = (int)groups.size();
 
-    // ---- capture [reset, persistent kernel, combine] in a graph
-    cudaStream_t cs = nullptr;
+    // ---- capture [reset, the groups' persistent kernels on parallel
+    // branches (groups dealt round-robin in execution order), combine]
+    constexpr int kBranches = 4;
+    const int nbr = std::min<int>(kBranches, (int)groups.size());
+    cudaStream_t cs = nullptr, br[kBranches] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kBranches] = {};
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int i = 0; i < nbr && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+    for (int i = 0; i < nbr && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), cs);
-    if (e == cudaSuccess && b->n_tiles)
-        e = b->prec ? q2x::batch_launch_f32(a, b->grid, b->smem, cs) : q2x::batch_launch_f64(a, b->grid, b->smem, cs);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long) * std::max<size_t>(1, groups.size()), cs);
+    if (e == cudaSuccess && nbr > 0) {
+        e = cudaEventRecord(ev_fork, cs);
+        for (int i = 0; i < nbr && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(br[i], ev_fork, 0);
+        for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
+            const Group& gr = groups[g];
+            e = fns[gr.combo * 5 + gr.bin].launch(a, gr.t0, gr.t1, (int)g, gr.grid, br[g % nbr]);
+        }
+        for (int i = 0; i < nbr && e == cudaSuccess; ++i) e = cudaEventRecord(ev_join[i], br[i]);
+        for (int i = 0; i < nbr && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(cs, ev_join[i], 0);
+    }
     if (e == cudaSuccess) {
         const int warps = 8;
         q2x::q2x_batch_combine<<<(unsigned)((nl + warps - 1) / warps), warps * 32, 0, cs>>>(
@@ -237,6 +268,11 @@ q2x_status build_batch(q2x_plan_t plan, const q2x_batch_desc* d, int tile_elems,
         cudaGraphDestroy(g);
     }
     if (cs) cudaStreamDestroy(cs);
+    for (int i = 0; i < nbr; ++i) {
+        if (br[i]) cudaStreamDestroy(br[i]);
+        if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_batch(b);
@@ -262,7 +298,7 @@ q2x_status q2x_batch_run(q2x_batch_t b)
     cudaSetDevice(b->plan->device);
     cudaError_t e = cudaGraphLaunch(b->exec, b->plan->stream);
     if (e != cudaSuccess) return q2x_cuda_fail(b->plan, e, "batch: cudaGraphLaunch");
-    b->plan->launches += (b->n_tiles ? 2 : 1);
+    b->plan->launches += b->n_groups + 1;
     return Q2X_OK;
 }
 

@@ -1,21 +1,15 @@
-// The persistent batch kernel, f64 instance (see q2x_batch.cuh).
+// The per-group persistent batch kernels, FP64 instances (see q2x_batch.cuh).
 #include "q2x_batch.cuh"
 
 namespace q2x {
 
-cudaError_t batch_launch_f64(const BatchArgs& b, int grid, size_t smem, cudaStream_t st)
+const BatchGroupFns* batch_group_table_f64()
 {
-    cudaError_t e = cudaFuncSetAttribute(q2x_batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    q2x_batch_kernel<double><<<grid, BATCH_WARPS * 32, smem, st>>>(b);
-    return cudaGetLastError();
-}
-
-cudaError_t batch_occupancy_f64(int* blocks_per_sm, size_t smem)
-{
-    cudaError_t e = cudaFuncSetAttribute(q2x_batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, q2x_batch_kernel<double>, BATCH_WARPS * 32, smem);
+    static const BatchGroupFns t[4][5] = {Q2X_BATCH_FNS_ROW(double, KIND_SEG, DENS_CONST),
+                                          Q2X_BATCH_FNS_ROW(double, KIND_TRI, DENS_CONST),
+                                          Q2X_BATCH_FNS_ROW(double, KIND_TRI, DENS_LINEAR),
+                                          Q2X_BATCH_FNS_ROW(double, KIND_TET, DENS_CONST)};
+    return &t[0][0];
 }
 
 }  // namespace q2x

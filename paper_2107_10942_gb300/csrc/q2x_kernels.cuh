@@ -1649,14 +1649,16 @@ __global__ void __launch_bounds__(elem_warps_per_cta<T>() * 32, (min_ctas<T, P, 
 }
 
 // Combine the slot partials of leaves that span several warp ranges.  One warp
-// per range boundary w (1 <= w < n_ranges) and block of 32 columns
-// (blockIdx.y): the leaf L containing element w*T is handled there iff w is
-// the last range L touches.  A lane sums its column's FP64 partials of the
-// ranges wf..w (partial i of the leaf into accumulator i mod 4, each a
-// compensated Neumaier sum, the four combined in a fixed order: the result
-// does not depend on scheduling), then scales the total like a complete run.
-// The four chains and the column blocks keep the dependent FP64 adds short
-// when a small problem's leaf spans tens of ranges.
+// per range boundary w (1 <= w < n_ranges) and block row (blockIdx.y, blocks
+// of 32 columns strided by gridDim.y): the leaf L containing element w*T is
+// handled there iff w is the last range L touches.  A lane sums its column's
+// FP64 partials of the ranges wf..w as compensated (Neumaier) sums in a fixed
+// order, so that the result does not depend on scheduling: one chain for a
+// leaf over at most 8 ranges, else partial i into accumulator i mod 4 and the
+// four combined in order.  Then it scales the total like a complete run.  The
+// four chains and, for few ranges, one block row per 32 columns keep the
+// dependent FP64 adds short when a small problem's leaf spans tens of ranges
+// (each FP64 add holds the sub-partition's FP64 pipe for about 64 cycles).
 static __global__ void q2x_fixup_kernel(const ElemArgs a, int d0, int d1, int d2, int s0, int s1, int s2)
 {
     const int lane = threadIdx.x & 31;
@@ -1669,8 +1671,6 @@ static __global__ void q2x_fixup_kernel(const ElemArgs a, int d0, int d1, int d2
     if (o0 >= e) return;                 // starts in this range: not spanning here
     if ((o1 - 1) / a.T != w) return;     // not the last range of L
     const int np = a.np_max;
-    const int c = (int)blockIdx.y * 32 + lane;
-    if (c >= np) return;
     const int64_t wf = o0 / a.T;
     const int slot_first = (o0 == wf * a.T) ? 0 : 1;
     const int s = a.leaf_rho ? scale_exponent(__ldg(a.leaf_rho + L)) : 0;
@@ -1679,55 +1679,68 @@ static __global__ void q2x_fixup_kernel(const ElemArgs a, int d0, int d1, int d2
         pl = __ldg(a.leaf_p + L);
         if (pl < 0 || pl > a.p_max) pl = -1;
     }
-    const int desc = col_desc(c);
     const double* slots = a.slots;
-    for (int ly = 0; ly < a.nacc; ++ly) {
-        if (a.coef[ly] == nullptr) continue;
-        // partial i: range wf + i (slot slot_first for i = 0, else slot 0)
-        auto partial = [&](int64_t i) {
-            const int64_t row = (i == 0) ? wf * 2 + slot_first : (wf + i) * 2;
-            return __ldg(slots + (row * a.nacc + ly) * (int64_t)np + c);
-        };
-        double sum[4] = {0.0, 0.0, 0.0, 0.0}, comp[4] = {0.0, 0.0, 0.0, 0.0};
-        auto step = [](double& sm, double& cp, double x) {  // Neumaier
-            const double t = sm + x;
-            if (fabs(sm) >= fabs(x))
-                cp += (sm - t) + x;
+    for (int c = (int)blockIdx.y * 32 + lane; c < np; c += (int)gridDim.y * 32) {
+        const int desc = col_desc(c);
+        for (int ly = 0; ly < a.nacc; ++ly) {
+            if (a.coef[ly] == nullptr) continue;
+            // partial i: range wf + i (slot slot_first for i = 0, else slot 0)
+            auto partial = [&](int64_t i) {
+                const int64_t row = (i == 0) ? wf * 2 + slot_first : (wf + i) * 2;
+                return __ldg(slots + (row * a.nacc + ly) * (int64_t)np + c);
+            };
+            auto step = [](double& sm, double& cp, double x) {  // Neumaier
+                const double t = sm + x;
+                if (fabs(sm) >= fabs(x))
+                    cp += (sm - t) + x;
+                else
+                    cp += (x - t) + sm;
+                sm = t;
+            };
+            const int64_t K = w - wf + 1;  // partials of the leaf
+            double tot, tc = 0.0;
+            if (K <= 8) {
+                // a leaf over a few ranges (large problems): one chain
+                tot = partial(0);
+                for (int64_t i = 1; i < K; ++i) step(tot, tc, partial(i));
+            } else {
+                double sum[4] = {0.0, 0.0, 0.0, 0.0}, comp[4] = {0.0, 0.0, 0.0, 0.0};
+                int64_t i = 0;
+                for (; i + 4 <= K; i += 4) {
+                    double x[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) x[u] = partial(i + u);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) step(sum[u], comp[u], x[u]);
+                }
+                for (int u = 0; i < K; ++i, ++u) step(sum[u], comp[u], partial(i));
+                tot = sum[0];
+                tc = comp[0] + comp[1] + comp[2] + comp[3];
+                for (int u = 1; u < 4; ++u) step(tot, tc, sum[u]);
+            }
+            tot += tc;
+            const double v = ((desc & 31) <= pl)
+                                 ? finish_desc(tot, a.norm, desc, ly == 0 ? d0 : ly == 1 ? d1 : d2,
+                                               ly == 0 ? s0 : ly == 1 ? s1 : s2, s)
+                                 : 0.0;
+            double* dst = a.coef[ly] + L * np + c;
+            if (a.accumulate)
+                *dst += v;
             else
-                cp += (x - t) + sm;
-            sm = t;
-        };
-        const int64_t K = w - wf + 1;  // partials of the leaf
-        int64_t i = 0;
-        for (; i + 4 <= K; i += 4) {
-            double x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = partial(i + u);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) step(sum[u], comp[u], x[u]);
+                *dst = v;
         }
-        for (int u = 0; i < K; ++i, ++u) step(sum[u], comp[u], partial(i));
-        double tot = sum[0], tc = comp[0] + comp[1] + comp[2] + comp[3];
-        for (int u = 1; u < 4; ++u) step(tot, tc, sum[u]);
-        tot += tc;
-        const double v = ((desc & 31) <= pl)
-                             ? finish_desc(tot, a.norm, desc, ly == 0 ? d0 : ly == 1 ? d1 : d2,
-                                           ly == 0 ? s0 : ly == 1 ? s1 : s2, s)
-                             : 0.0;
-        double* dst = a.coef[ly] + L * np + c;
-        if (a.accumulate)
-            *dst += v;
-        else
-            *dst = v;
     }
 }
 
 // The fix-up launch for a range split (n_ranges > 1): 4 warps per block over
-// the boundaries, one block row per 32 columns.
+// the boundaries; with few boundaries (a small problem, whose leaves can span
+// many ranges) one block row per 32 columns, else one row looping over them
+// (each warp's leaf search is then done once).
 inline cudaError_t launch_fixup(const ElemArgs& a, cudaStream_t st, int d0, int d1, int d2, int s0, int s1, int s2)
 {
     if (a.n_ranges <= 1) return cudaSuccess;
-    const dim3 grid((unsigned)((a.n_ranges - 1 + 3) / 4), (unsigned)((a.np_max + 31) / 32));
+    const unsigned rows = (a.n_ranges <= 257) ? (unsigned)((a.np_max + 31) / 32) : 1u;
+    const dim3 grid((unsigned)((a.n_ranges - 1 + 3) / 4), rows);
     q2x_fixup_kernel<<<grid, 128, 0, st>>>(a, d0, d1, d2, s0, s1, s2);
     return cudaGetLastError();
 }
