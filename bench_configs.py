@@ -130,7 +130,8 @@ def run_mixed_ball(args, dev):
                                                               ("segment", "triangle", "tetra")] +
                                                              [m["leaf_c"].shape[1]]),
                       "tiles": info["tiles"], "tile_elems": info["tile_elems"],
-                      "launch": "one CUDA-graph replay (counter reset, persistent kernel, combine)"},
+                      "launch": "one CUDA-graph replay (counter reset, one persistent kernel per (kind, degree "
+                                "bin) group of tiles on four parallel branches, combine)"},
            "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAKS["fp32"] / 1e12,
                         "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAKS["fp32"],
                         "note": "whole graph replay (reset + persistent kernel + combine) as the duration"},

@@ -284,28 +284,21 @@ __device__ __forceinline__ cf cf_zero()
 // are formed once per row entry and shared by every stencil applied to it
 // (the output level and its double layer).
 struct cf_nb {
-    cf d, sw;  // b - a and swap(a + b)
+    cf d, s;  // b - a and a + b (both packed)
 };
-__device__ __forceinline__ cf_nb cf_neighbours(cf a, cf b)
-{
-    // swap(a + b) as two scalar adds
-    float ar, ai, br, bi;
-    cf_parts(a, ar, ai);
-    cf_parts(b, br, bi);
-    return cf_nb{cf_sub(b, a), cf_make(bi + ai, br + ar)};
-}
+__device__ __forceinline__ cf_nb cf_neighbours(cf a, cf b) { return cf_nb{cf_sub(b, a), cf_add(a, b)}; }
 __device__ __forceinline__ cf cf_stencil_nb(const cf_nb& nb, cf c, cf src, cf X2, cf YmY, cf nZ2)
 {
     cf t = cf_fma(nZ2, c, src);
     t = cf_fma(X2, nb.d, t);
-    // the Y term as two scalar FMAs on the halves: its operand swap(a + b)
-    // is made of scalar sums, and forming it into a register pair for a
-    // paired FMA costs more than the extra instruction (measured)
+    // the Y term as two scalar FMAs that read the halves of a + b crosswise
+    // (the swap costs no instruction); forming swap(a + b) into a register
+    // pair for a paired FMA costs more than the extra FMA (measured)
     float tr, ti, sr, si, yy, ny;
     cf_parts(t, tr, ti);
-    cf_parts(nb.sw, sr, si);
+    cf_parts(nb.s, sr, si);
     cf_parts(YmY, yy, ny);
-    return cf_make(fmaf(yy, sr, tr), fmaf(ny, si, ti));
+    return cf_make(fmaf(yy, si, tr), fmaf(ny, sr, ti));
 }
 
 // column c -> (n, m), exact for c < 2^20
@@ -1383,15 +1376,17 @@ struct ElemCfg {
 // Resident CTAs per SM the element kernel is compiled for, which caps its
 // registers: FP32 chains whose rows leave room run 4 warps per sub-partition
 // (segments up to P = 16, constant-density single-layer triangles up to
-// P = 8) or 3 (those triangles up to P = 16), without spills; the rest, and
-// FP64, 2 warps per sub-partition (no cap below 255 registers).
+// P = 8) or 3 (segments at P = 20, those triangles up to P = 20; at most 4
+// bytes of spill stores), the rest, and FP64, 2 warps per sub-partition (no
+// cap below 255 registers).
 template <typename T, int P, int KIND, int DENS, int OUTS>
 __host__ __device__ constexpr int min_ctas()
 {
     if constexpr (sizeof(T) == 4) {
         if (KIND == KIND_SEG && OUTS == 1 && P <= 16) return 16;
+        if (KIND == KIND_SEG && OUTS == 1) return 12;
         if (KIND == KIND_TRI && DENS == DENS_CONST && OUTS == 1 && P <= 8) return 16;
-        if (KIND == KIND_TRI && DENS == DENS_CONST && OUTS == 1 && P <= 16) return 12;
+        if (KIND == KIND_TRI && DENS == DENS_CONST && OUTS == 1) return 12;
         return 8;
     } else {
         return 2;

@@ -168,6 +168,20 @@ def test_accumulate_mixed_kinds(q2x, orc, prec):
     assert norm_err(coef.cpu().numpy(), ref, 8, rho, 0) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_leaf_over_many_ranges(q2x, orc, prec):
+    # with about 2,200 elements every warp range holds 32 of them, so the
+    # 1,500-element leaf spans some 47 ranges (the fix-up's four-chain sums)
+    # and the 70-element one three (its single chain); run twice: bit-equal
+    prob = random_problem("triangle", [1500, 3, 0, 70, 600], seed=41, p=8, density="const")
+    a = run(q2x, prob, prec, single=True, double=True)
+    b = run(q2x, prob, prec, single=True, double=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for layer in (0, 1):
+        e = norm_err(a[layer], oracle_coef(orc, prob, layer=layer), 8, prob["leaf_rho"], layer)
+        assert e <= TOL[prec], (layer, e)
+
+
 def test_deterministic(q2x):
     prob = random_problem("triangle", SIZES * 3, seed=2, p=12, density="linear")
     for prec in ("fp64", "fp32"):
