@@ -64,9 +64,9 @@ DEFAULT_WORKLOAD = "sphere-L9-const"
 # the packed instructions are not in the FFMA/FADD class counters).
 KERNEL_COUNTERS = {
     ("sphere-L9-const", "fp64"): dict(traffic=218551296 + 112463104, executed_flops=35642946312),
-    ("sphere-L9-const", "fp32"): {},
+    ("sphere-L9-const", "fp32"): dict(traffic=222476544 + 112289536, executed_flops=41174190806),
     ("sphere-L7-linear", "fp64"): dict(traffic=9513984 + 1454848, executed_flops=2863254784),
-    ("sphere-L7-linear", "fp32"): {},
+    ("sphere-L7-linear", "fp32"): dict(traffic=9379584 + 768, executed_flops=3403618476),
 }
 COUNTER_SOURCE = "ncu --set full capture of one launch of this kernel on this workload"
 
