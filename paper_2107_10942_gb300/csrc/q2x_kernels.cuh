@@ -1051,7 +1051,7 @@ __device__ __forceinline__ void load_frame(const double* __restrict__ vx, const 
 //
 // FP64: the rows of levels k < NS live in shared memory (srows, [NS][P + 1][32]
 // complex entries, one 16-byte entry per lane and order) instead of registers;
-// see smem_levels.
+// ElemCfg chooses NS and the stage-tile width CH.
 template <typename T, int P, int KIND, int DENS, int OUTS, bool WIDE = false, int NS = 0,
           int CH = KCfg<T>::CHUNK, typename Reduce>
 __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>& F, int pw, T* tile,
