@@ -1,6 +1,7 @@
-"""GPU tests of the ragged mixed batch (q2x_batch_*): one persistent launch in
-a CUDA graph over segments, triangles and tetrahedra sharing an adaptive
-octree with per-leaf degrees, checked against the oracle (sum over kinds)."""
+"""GPU tests of the ragged mixed batch (q2x_batch_*): one CUDA-graph replay
+(a persistent kernel per kind and degree bin) over segments, triangles and
+tetrahedra sharing an adaptive octree with per-leaf degrees, checked against
+the oracle (sum over kinds)."""
 import json
 
 import numpy as np
