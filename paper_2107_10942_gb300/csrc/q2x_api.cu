@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "q2x.h"
+#include "q2x_batch.cuh"
 #include "q2x_kernels.cuh"
 #include "q2x_plan.h"
 
@@ -260,6 +261,21 @@ __global__ void leaf_reduce_weighted_kernel(const double* __restrict__ elem, int
 
 // --------------------------------------------------------------- dispatch
 
+// Elements per leaf tile of the FP32-mixed single-layer path.
+constexpr int64_t kLeafTileElems = 256;
+
+// workspace of the leaf-tile path (after the per-leaf scales): the tile list,
+// the scans, and the partial rows of leaves of several tiles
+size_t leaf_tile_ws_bytes(int64_t n_elem, int64_t n_leaves, int np)
+{
+    const int64_t nb = q2x::leaf_tile_blocks(n_leaves);
+    const int64_t mt = q2x::leaf_tile_max_tiles(n_leaves, n_elem, kLeafTileElems);
+    const int64_t ms = q2x::leaf_tile_max_slots(n_elem, kLeafTileElems);
+    return align_up(sizeof(q2x::BatchTile) * (size_t)mt, 256) + 2 * align_up(sizeof(int64_t) * (size_t)n_leaves, 256) +
+           2 * align_up(sizeof(int64_t) * (size_t)nb, 256) + align_up(sizeof(int64_t) * (size_t)(n_leaves + 1), 256) +
+           256 + 256 + align_up(sizeof(double) * (size_t)ms * np, 256);
+}
+
 q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int64_t n_vert,
                         const double* vxyz, const int32_t* idx, const double* sigma,
                         int64_t n_leaves, const int64_t* leaf_off, const double* leaf_c,
@@ -321,6 +337,12 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
         if (e != cudaSuccess) return cuda_fail(plan, e, "occupancy query");
         if (occ <= 0) return fail(plan, Q2X_ERR_CUDA, "kernel does not fit on the device (smem %zu)", ke.smem(np));
     }
+    // FP32-mixed single layer in leaf mode: leaf tiles through the batch's
+    // persistent tile kernel (q2x_tiles.cu): a round holds one leaf's elements,
+    // so every staged chunk is summed pairwise, with no leaf-boundary work in
+    // the degree loop, and warps pull tiles from a counter
+    const bool tiles = prec == 1 && leaf_off && !vec && coef0 && !(kind == q2x::KIND_TRI && coef1) &&
+                       n_leaves < ((int64_t)1 << 31);
     const int64_t resident_warps = (int64_t)occ * wpc * plan->num_sms;
     // one range per resident warp (ranges need not be multiples of 32: rounds
     // are formed per leaf inside the kernel), at least one full round each
@@ -330,10 +352,11 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
 
     // workspace: slots, then per-leaf scale (FP32 without leaf_rho)
     const bool need_rho = prec == 1 && leaf_rho == nullptr;
-    const size_t slot_bytes = align_up(sizeof(double) * (size_t)n_ranges * 2 * nacc * np, 256);  // FP64 partials
+    const size_t slot_bytes = tiles ? 0 : align_up(sizeof(double) * (size_t)n_ranges * 2 * nacc * np, 256);  // FP64 partials
     const size_t rho_bytes = need_rho ? align_up(sizeof(double) * (size_t)n_leaves, 256) : 0;
     const size_t bits_bytes = need_rho ? align_up(sizeof(int) * (size_t)n_leaves, 256) : 0;
-    q2x_status st = ensure_ws(plan, slot_bytes + rho_bytes + bits_bytes);
+    const size_t tile_bytes = tiles ? leaf_tile_ws_bytes(n_elem, n_leaves, np) : 0;
+    q2x_status st = ensure_ws(plan, slot_bytes + rho_bytes + bits_bytes + tile_bytes);
     if (st != Q2X_OK) return st;
     unsigned char* ws = static_cast<unsigned char*>(plan->ws);
 
@@ -352,6 +375,82 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
         rho_bits_to_double<<<(unsigned)((n_leaves + 255) / 256), 256, 0, plan->stream>>>(bits, rho, n_leaves);
         plan->launches += 2;
         leaf_rho = rho;
+    }
+
+    if (tiles) {
+        unsigned char* p = ws + slot_bytes + rho_bytes + bits_bytes;
+        auto take = [&](size_t bytes) {
+            unsigned char* q = p;
+            p += align_up(bytes, 256);
+            return q;
+        };
+        const int64_t nb = q2x::leaf_tile_blocks(n_leaves);
+        const int64_t mt = q2x::leaf_tile_max_tiles(n_leaves, n_elem, kLeafTileElems);
+        const int64_t ms = q2x::leaf_tile_max_slots(n_elem, kLeafTileElems);
+        q2x::LeafTileWork w;
+        w.tiles = reinterpret_cast<q2x::BatchTile*>(take(sizeof(q2x::BatchTile) * (size_t)mt));
+        w.tile_pre = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * (size_t)n_leaves));
+        w.slot_pre = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * (size_t)n_leaves));
+        w.block_tiles = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * (size_t)nb));
+        w.block_slots = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * (size_t)nb));
+        w.slot_off = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * (size_t)(n_leaves + 1)));
+        w.n_tiles = reinterpret_cast<int64_t*>(take(sizeof(int64_t)));
+        w.counter = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long)));
+        double* partial = reinterpret_cast<double*>(take(sizeof(double) * (size_t)ms * np));
+        w.max_tiles = mt;
+        w.max_slots = ms;
+        w.n_elem = n_elem;
+        const int tcombo = (kind == q2x::KIND_SEG) ? 0 : (kind == q2x::KIND_TET) ? 3 : (dens == Q2X_DENSITY_LINEAR ? 2 : 1);
+        const q2x::BatchGroupFns& f = q2x::batch_group_table_f32()[tcombo * 5 + bin];
+        int& tocc = plan->tile_occ[tcombo][bin];
+        if (tocc == 0) {
+            e = f.occupancy(&tocc);
+            if (e != cudaSuccess) return cuda_fail(plan, e, "tile kernel occupancy query");
+            if (tocc <= 0) return fail(plan, Q2X_ERR_CUDA, "tile kernel does not fit on the device (smem %zu)", f.smem);
+        }
+        e = q2x::leaf_tiles_build(leaf_off, n_leaves, kLeafTileElems, tcombo, bin, w, plan->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.counter, 0, sizeof(unsigned long long), plan->stream);
+        if (e != cudaSuccess) return cuda_fail(plan, e, "leaf tile list");
+        q2x::BatchArgs b{};
+        b.kind[kind].n_elem = n_elem;
+        b.kind[kind].n_vert = n_vert;
+        b.kind[kind].vx = vxyz;
+        b.kind[kind].vy = vxyz + n_vert;
+        b.kind[kind].vz = vxyz + 2 * n_vert;
+        b.kind[kind].idx = idx;
+        b.kind[kind].sigma = sigma;
+        b.n_leaves = n_leaves;
+        b.leaf_c = leaf_c;
+        b.leaf_rho = leaf_rho;
+        b.leaf_p = leaf_p;
+        b.p_max = plan->p_max;
+        b.np_max = np;
+        b.norm = plan->norm;
+        b.tiles = w.tiles;
+        b.n_tiles = 0;
+        b.counter = w.counter;
+        b.partial = partial;
+        b.err = plan->d_err;
+        b.coef = coef0;
+        b.accumulate = accumulate;
+        b.n_tiles_dev = w.n_tiles;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (plan->timing) {
+            st = take_event(plan, &ev0);
+            if (st == Q2X_OK) st = take_event(plan, &ev1);
+            if (st != Q2X_OK) return st;
+            cudaEventRecord(ev0, plan->stream);
+        }
+        e = f.launch(b, 0, -1, 0, tocc * plan->num_sms, plan->stream);
+        if (e != cudaSuccess) return cuda_fail(plan, e, "tile kernel launch");
+        if (plan->timing) {
+            cudaEventRecord(ev1, plan->stream);
+            plan->ev_pending.emplace_back(ev0, ev1);
+        }
+        e = q2x::leaf_tiles_combine(partial, w.slot_off, leaf_off, np, n_leaves, coef0, accumulate, plan->stream);
+        if (e != cudaSuccess) return cuda_fail(plan, e, "leaf tile combine");
+        plan->launches += 5;
+        return Q2X_OK;
     }
 
     q2x::ElemArgs a;
@@ -551,8 +650,9 @@ q2x_status q2x_reserve(q2x_plan_t plan, int64_t n_elem, int64_t n_leaves)
     const int np = (plan->p_max + 1) * (plan->p_max + 1);
     // worst case: one range per 32 elements; FP64 partials in both precisions
     const int64_t n_ranges = (n_elem + 31) / 32;
-    const size_t bytes = align_up(sizeof(double) * (size_t)n_ranges * 2 * 3 * np, 256) +
-                         align_up(sizeof(double) * (size_t)n_leaves, 256) +
+    const size_t elem = align_up(sizeof(double) * (size_t)n_ranges * 2 * 3 * np, 256);
+    const size_t tile = plan->prec == 1 ? leaf_tile_ws_bytes(n_elem, n_leaves, np) : 0;
+    const size_t bytes = std::max(elem, tile) + align_up(sizeof(double) * (size_t)n_leaves, 256) +
                          align_up(sizeof(int) * (size_t)n_leaves, 256);
     return ensure_ws(plan, bytes);
 }

@@ -30,12 +30,14 @@ struct BatchKind {
 };
 
 // combo: 0 segments, 1 triangles constant density, 2 triangles linear
-// density, 3 tetrahedra; bin: index of the capacity P in {4, 8, 12, 16, 20}
+// density, 3 tetrahedra; bin: index of the capacity P in {4, 8, 12, 16, 20};
+// flags bit 0: the tile is its leaf's only one, and its finished row goes
+// straight to coef[leaf] (else to partial row slot, for the combine)
 struct BatchTile {
     int32_t combo;
     int32_t bin;
     int32_t leaf;
-    int32_t pad;
+    int32_t flags;
     int64_t slot;
     int64_t e_lo, e_hi;
 };
@@ -52,6 +54,9 @@ struct BatchArgs {
     unsigned long long* counter;  // one per group
     double* partial;  // [n_slots][np_max]
     unsigned* err;
+    double* coef;                 // rows of single-tile leaves (flags bit 0)
+    int accumulate;               // those rows are added to coef
+    const int64_t* n_tiles_dev;   // tile count on the device (a kernel launched with t1 < 0)
 };
 
 constexpr int BATCH_WARPS = 4;
@@ -116,19 +121,24 @@ __device__ __forceinline__ void batch_tile(const BatchArgs& b, const BatchTile& 
     }
     if (errbits) atomicOr(b.err, errbits);
     __syncwarp();
-    double* out = b.partial + t.slot * (int64_t)np;
+    const bool direct = (t.flags & 1) != 0;
+    double* out = direct ? b.coef + L * (int64_t)np : b.partial + t.slot * (int64_t)np;
+    const bool add = direct && b.accumulate;
     const int npl = (pL + 1) * (pL + 1);
 #pragma unroll 1
     for (int c = lane; c < np; c += 32) {
         double v = 0.0;
         if (c < npl) v = finish_desc(accb[c].rounded(), b.norm, col_desc(c), C::D_OUT, KIND + 1, sexp);
-        out[c] = v;
+        if (add)
+            out[c] += v;
+        else
+            out[c] = v;
     }
     __syncwarp();
 }
 
-// The persistent kernel of one group: tiles t0 .. t1-1 of the sorted list,
-// pulled through the group's counter g.
+// The persistent kernel of one group: tiles t0 .. t1-1 of the sorted list
+// (t1 < 0: t0 .. t0 + *n_tiles_dev - 1), pulled through the group's counter g.
 template <typename T, int P, int KIND, int DENS>
 __global__ void __launch_bounds__(BATCH_WARPS * 32, (BatchCfg<T, P, KIND, DENS>::MIN_CTAS))
     q2x_batch_group_kernel(const BatchArgs b, int64_t t0, int64_t t1, int g)
@@ -140,12 +150,13 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, (BatchCfg<T, P, KIND, DENS>:
     unsigned char* wsm = smem_raw + (size_t)wib * BC::WARP_BYTES;
     T* tile = reinterpret_cast<T*>(wsm);
     LeafSum<T>* accb = reinterpret_cast<LeafSum<T>*>(tile + 2 * BC::CH * KCfg<T>::LD);  // 2 CH LD sizeof(T) % 8 == 0
+    const int64_t nt = (t1 < 0) ? __ldg(b.n_tiles_dev) : t1 - t0;
 #pragma unroll 1
     while (true) {
         unsigned long long ti = 0;
         if (lane == 0) ti = atomicAdd(b.counter + g, 1ull);
         ti = __shfl_sync(0xffffffffu, ti, 0);
-        if (ti >= (unsigned long long)(t1 - t0)) break;
+        if (ti >= (unsigned long long)nt) break;
         const BatchTile t = b.tiles[t0 + (int64_t)ti];
         batch_tile<T, P, KIND, DENS, BC::CH>(b, t, tile, accb, lane);
     }
@@ -196,5 +207,35 @@ const BatchGroupFns* batch_group_table_f64();
 // coef[L] (+)= sum of the partial rows slot_off[L] .. slot_off[L+1]-1, in order
 __global__ void q2x_batch_combine(const double* __restrict__ partial, const int64_t* __restrict__ slot_off,
                                   int np, int64_t n_leaves, double* coef, int accumulate);
+
+// ---- Leaf tiles of one element set (q2x_tiles.cu): the single-layer FP32
+// path of the element calls.  Every leaf of n_L > 0 elements becomes
+// ceil(n_L / T) tiles of one kind and degree bin (balanced sizes); a leaf of
+// one tile writes its row straight to coef, a leaf of several sums its tiles'
+// rows in the combine.  All on the device, in stream order: no host
+// synchronisation, so the call stays capturable in a CUDA graph.
+struct LeafTileWork {
+    BatchTile* tiles;       // [max_tiles]
+    int64_t* tile_pre;      // [n_leaves]: a leaf's first tile within its block of leaves
+    int64_t* slot_pre;      // [n_leaves]: its first partial row within the block
+    int64_t* block_tiles;   // [n_blocks] (then their exclusive prefix)
+    int64_t* block_slots;   // [n_blocks]
+    int64_t* slot_off;      // [n_leaves + 1]: partial rows of each multi-tile leaf
+    int64_t* n_tiles;       // [1]
+    unsigned long long* counter;  // [1]
+    int64_t max_tiles, max_slots; // buffer sizes: tiles and partial rows past them are dropped
+    int64_t n_elem;               // element ranges are clamped to [0, n_elem)
+};
+constexpr int kLeafTileBlock = 1024;  // leaves per block of the tile count
+inline int64_t leaf_tile_blocks(int64_t n_leaves) { return (n_leaves + kLeafTileBlock - 1) / kLeafTileBlock; }
+inline int64_t leaf_tile_max_tiles(int64_t n_leaves, int64_t n_elem, int64_t T) { return n_leaves + (n_elem + T - 1) / T; }
+inline int64_t leaf_tile_max_slots(int64_t n_elem, int64_t T) { return 2 * ((n_elem + T - 1) / T); }
+// tile list of leaf_off with at most T elements per tile
+cudaError_t leaf_tiles_build(const int64_t* leaf_off, int64_t n_leaves, int64_t T, int combo, int bin,
+                             const LeafTileWork& w, cudaStream_t st);
+// coef rows of the multi-tile leaves (sum of their partial rows in order) and,
+// unless accumulating, zero rows for empty leaves
+cudaError_t leaf_tiles_combine(const double* partial, const int64_t* slot_off, const int64_t* leaf_off,
+                               int np, int64_t n_leaves, double* coef, int accumulate, cudaStream_t st);
 
 }  // namespace q2x

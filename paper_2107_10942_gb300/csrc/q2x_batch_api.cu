@@ -214,6 +214,9 @@ q2x_status build_batch(q2x_plan_t plan, const q2x_batch_desc* d, int tile_elems,
     a.counter = b->d_counter;
     a.partial = b->d_partial;
     a.err = plan->d_err;
+    a.coef = b->coef;  // unused here: every tile has a partial row (flags 0)
+    a.accumulate = b->accumulate;
+    a.n_tiles_dev = nullptr;
     const q2x::BatchGroupFns* fns = b->prec ? q2x::batch_group_table_f32() : q2x::batch_group_table_f64();
     for (Group& gr : groups) {
         const q2x::BatchGroupFns& f = fns[gr.combo * 5 + gr.bin];

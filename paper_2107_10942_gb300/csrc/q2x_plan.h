@@ -21,6 +21,7 @@ struct q2x_plan_s {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     int occ_cache[2][9][5] = {};  // [precision][element combo][capacity bin]
+    int tile_occ[4][5] = {};  // resident CTAs per SM of the FP32 leaf-tile kernels [combo][bin]
     int timing = 0;
     std::vector<cudaEvent_t> ev_pool;                            // idle events
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded pairs
