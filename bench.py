@@ -57,14 +57,17 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "sphere-L9-const"
 
 # Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) and
-# executed flops of the element kernels, from one ncu capture of the current
-# kernel on each workload (None: not captured since the kernel last changed).
+# executed flops of the dominant kernel of each arm (the element kernel; for
+# the FP32-mixed single layer, the leaf-tile kernel), from one ncu capture of
+# the current kernel on each workload (empty: not captured since the kernel
+# last changed).  The leaf-tile kernel's executed count includes the idle
+# lanes of rounds that a leaf fills only partly.
 # Executed flops: FP64 2 x DFMA + DADD + DMUL thread instructions; FP32
 # 4 x FFMA2 + 2 x FFMA + 2 x FADD2 + 2 x FMUL2 + FADD + FMUL (per-opcode thread counts:
 # the packed instructions are not in the FFMA/FADD class counters).
 KERNEL_COUNTERS = {
     ("sphere-L9-const", "fp64"): dict(traffic=218551296 + 112463104, executed_flops=35642946312),
-    ("sphere-L9-const", "fp32"): {},
+    ("sphere-L9-const", "fp32"): dict(traffic=178060800 + 104677888, executed_flops=48086597700),
     ("sphere-L7-linear", "fp64"): dict(traffic=9513984 + 1454848, executed_flops=2863254784),
     ("sphere-L7-linear", "fp32"): dict(traffic=9379584 + 768, executed_flops=3403618476),
 }
