@@ -341,8 +341,10 @@ q2x_status run_elements(q2x_plan_t plan, int kind, int dens, int64_t n_elem, int
     // persistent tile kernel (q2x_tiles.cu): a round holds one leaf's elements,
     // so every staged chunk is summed pairwise, with no leaf-boundary work in
     // the degree loop, and warps pull tiles from a counter
+    // (its workspace bound assumes every tile needs a partial row: beyond
+    // 8 GiB the element kernel, whose workspace is per warp range, runs)
     const bool tiles = prec == 1 && leaf_off && !vec && coef0 && !(kind == q2x::KIND_TRI && coef1) &&
-                       n_leaves < ((int64_t)1 << 31);
+                       n_leaves < ((int64_t)1 << 31) && leaf_tile_ws_bytes(n_elem, n_leaves, np) <= ((size_t)8 << 30);
     const int64_t resident_warps = (int64_t)occ * wpc * plan->num_sms;
     // one range per resident warp (ranges need not be multiples of 32: rounds
     // are formed per leaf inside the kernel), at least one full round each
@@ -651,7 +653,8 @@ q2x_status q2x_reserve(q2x_plan_t plan, int64_t n_elem, int64_t n_leaves)
     // worst case: one range per 32 elements; FP64 partials in both precisions
     const int64_t n_ranges = (n_elem + 31) / 32;
     const size_t elem = align_up(sizeof(double) * (size_t)n_ranges * 2 * 3 * np, 256);
-    const size_t tile = plan->prec == 1 ? leaf_tile_ws_bytes(n_elem, n_leaves, np) : 0;
+    size_t tile = plan->prec == 1 ? leaf_tile_ws_bytes(n_elem, n_leaves, np) : 0;
+    if (tile > ((size_t)8 << 30)) tile = 0;  // such calls run the element kernel
     const size_t bytes = std::max(elem, tile) + align_up(sizeof(double) * (size_t)n_leaves, 256) +
                          align_up(sizeof(int) * (size_t)n_leaves, 256);
     return ensure_ws(plan, bytes);
