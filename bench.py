@@ -67,9 +67,9 @@ DEFAULT_WORKLOAD = "sphere-L9-const"
 # the packed instructions are not in the FFMA/FADD class counters).
 KERNEL_COUNTERS = {
     ("sphere-L9-const", "fp64"): dict(traffic=218551296 + 112463104, executed_flops=35642946312),
-    ("sphere-L9-const", "fp32"): dict(traffic=178060800 + 104677888, executed_flops=48086597700),
+    ("sphere-L9-const", "fp32"): dict(traffic=177844224 + 104552192, executed_flops=47011848132),
     ("sphere-L7-linear", "fp64"): dict(traffic=9513984 + 1454848, executed_flops=2863254784),
-    ("sphere-L7-linear", "fp32"): dict(traffic=9379584 + 768, executed_flops=3403618476),
+    ("sphere-L7-linear", "fp32"): dict(traffic=9379072 + 512, executed_flops=3266600364),
 }
 COUNTER_SOURCE = "ncu --set full capture of one launch of this kernel on this workload"
 

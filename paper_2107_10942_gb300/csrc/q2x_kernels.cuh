@@ -615,13 +615,30 @@ __device__ __forceinline__ T tree8(const T (&s)[8], int g0, int g1)
     return ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
 }
 
-// Sum of all 32 rows of a column (the single-leaf tiles of the batch kernel).
+// Sum of all 32 rows of a column (the single-leaf tiles of the batch kernel)
+// as a fixed pairwise tree.  FP32: with paired adds, rows r and r + 2 of each
+// group of four first, then the groups pairwise, both halves at once (15
+// paired adds and one scalar add instead of 31 adds).
 template <typename T>
 __device__ __forceinline__ T sum_rows32(const T* col)
 {
     T s[8];
     group_sums(col, s);
     return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+template <>
+__device__ __forceinline__ float sum_rows32<float>(const float* col)
+{
+    float4 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = *reinterpret_cast<const float4*>(col + 4 * i);
+    cf a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = cf_add(cf_make(v[i].x, v[i].y), cf_make(v[i].z, v[i].w));
+    const cf d = cf_add(cf_add(cf_add(a[0], a[1]), cf_add(a[2], a[3])), cf_add(cf_add(a[4], a[5]), cf_add(a[6], a[7])));
+    float x, y;
+    cf_parts(d, x, y);
+    return x + y;
 }
 
 // Per-element expansions (no leaves): row r of a staged chunk is the complete
@@ -1080,9 +1097,9 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
     // are skipped by warp-uniform branches.
     int nb = 0;  // first degree of the chunk being staged
     if constexpr (FP32) {
-        // ---- FP32: packed complex arithmetic, blocks of MB orders (orders
-        // in (n, block end) are computed but stay exactly zero)
-        constexpr int MB = 2;
+        // ---- FP32: packed complex arithmetic, orders 0..n of each degree
+        // (the unrolled order loop leaves at the first order above n, one
+        // uniform branch per order; separate tests of every order cost 19 %)
         cf X2[NL], YmY[NL], nZ2[NL];
 #pragma unroll
         for (int k = 0; k < NL; ++k) {
@@ -1104,70 +1121,65 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
             const float c2f = (float)(n + 1) * (float)s2;
             const cf c2p = cf_make(c2f, c2f);
             const cf sd = cf_make((n == 0) ? (float)seed : 0.f, 0.f);
-            cf pa[NL];  // old x^{m-1} of each level
+            // The neighbours (b - a, a + b) of order m + 1 are formed at order
+            // m, before x^m is replaced: the new entry then takes the old
+            // one's register (formed at order m + 1, the old x^m would stay
+            // live beside the new one and cost a register copy per entry).
+            cf_nb nbn[NL];
 #pragma unroll
-            for (int mb = 0; mb <= P; mb += MB) {
-                if (mb <= n) {
+            for (int m = 0; m <= P; ++m) {
+                if (m > n) break;
+                cf nw[NL];
 #pragma unroll
-                    for (int m = mb; m < mb + MB && m <= P; ++m) {
-                        const bool st = (m <= n);
-                        cf nw[NL];
-#pragma unroll
-                        for (int k = 0; k < NL; ++k) {
-                            const cf c = R[k][m];
-                            const cf b = (m < P) ? R[k][m < P ? m + 1 : P] : cf_zero();
-                            // m = 0 (Eq. (rec11)): 2 Re(eta b) - z c + src, real; scalar
-                            float br0 = 0.f, bi0 = 0.f, cr0 = 0.f, ci0 = 0.f;
-                            if (m == 0) {
-                                cf_parts(b, br0, bi0);
-                                cf_parts(c, cr0, ci0);
-                            }
-                            const cf a = (m == 0) ? cf_zero() : pa[k];
-                            const cf_nb nbk = cf_neighbours(a, b);
-                            if (KIND == KIND_TRI && k == OUT && want1) {
-                                // double layer from the output level's row n-1
-                                float dr, di;
-                                if (m == 0) {
-                                    dr = fmaf(2.f * XN, br0, fmaf(2.f * YN, bi0, -ZN * cr0));
-                                    di = 0.f;
-                                } else {
-                                    cf dl = cf_stencil_nb(nbk, c, cf_zero(), XN2, YNm, nZN2);
-                                    cf_parts(dl, dr, di);
-                                }
-                                if (st) {
-                                    trow1[m * LD] = (m & 1) ? di : dr;
-                                    if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
-                                }
-                            }
-                            cf src;
-                            if (k == 0)
-                                src = (m == 0) ? sd : cf_zero();
-                            else if (LIN && k == 2)
-                                src = cf_fma(c2p, nw[0], cf_mul(s3p, nw[1]));  // (n+1) s2 q^ + s3 j^
-                            else if (LIN && k == 3)
-                                src = nw[1];  // i^ <- j^
-                            else if (LIN && k == 4)
-                                src = cf_fma(s1p, nw[3], nw[2]);  // E^ + s1 i^
-                            else
-                                src = nw[k > 0 ? k - 1 : 0];
-                            if (m == 0) {
-                                float sr0, si0;
-                                cf_parts(src, sr0, si0);
-                                nw[k] = cf_make(fmaf(2.f * LX[k], br0, fmaf(2.f * LY[k], bi0, fmaf(-LZ[k], cr0, sr0))),
-                                                0.f);
-                            } else {
-                                nw[k] = cf_stencil_nb(nbk, c, src, X2[k], YmY[k], nZ2[k]);
-                            }
-                            pa[k] = c;
-                            R[k][m] = nw[k];
-                        }
-                        if (want0 && st) {
-                            float vr, vi;
-                            cf_parts(nw[OUT], vr, vi);
-                            trow0[m * LD] = (m & 1) ? vi : vr;
-                            if (m > 0) trow0[-m * LD] = (m & 1) ? vr : vi;
-                        }
+                for (int k = 0; k < NL; ++k) {
+                    const cf c = R[k][m];
+                    // m = 0 (Eq. (rec11)): 2 Re(eta b) - z c + src, real; scalar
+                    float br0 = 0.f, bi0 = 0.f, cr0 = 0.f, ci0 = 0.f;
+                    if (m == 0) {
+                        const cf b = (P > 0) ? R[k][P > 0 ? 1 : 0] : cf_zero();
+                        cf_parts(b, br0, bi0);
+                        cf_parts(c, cr0, ci0);
                     }
+                    const cf_nb nbk = (m == 0) ? cf_nb{cf_zero(), cf_zero()} : nbn[k];
+                    if (m < P) nbn[k] = cf_neighbours(c, (m + 2 <= P) ? R[k][m + 2 <= P ? m + 2 : P] : cf_zero());
+                    if (KIND == KIND_TRI && k == OUT && want1) {
+                        // double layer from the output level's row n-1
+                        float dr, di;
+                        if (m == 0) {
+                            dr = fmaf(2.f * XN, br0, fmaf(2.f * YN, bi0, -ZN * cr0));
+                            di = 0.f;
+                        } else {
+                            cf dl = cf_stencil_nb(nbk, c, cf_zero(), XN2, YNm, nZN2);
+                            cf_parts(dl, dr, di);
+                        }
+                        trow1[m * LD] = (m & 1) ? di : dr;
+                        if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
+                    }
+                    cf src;
+                    if (k == 0)
+                        src = (m == 0) ? sd : cf_zero();
+                    else if (LIN && k == 2)
+                        src = cf_fma(c2p, nw[0], cf_mul(s3p, nw[1]));  // (n+1) s2 q^ + s3 j^
+                    else if (LIN && k == 3)
+                        src = nw[1];  // i^ <- j^
+                    else if (LIN && k == 4)
+                        src = cf_fma(s1p, nw[3], nw[2]);  // E^ + s1 i^
+                    else
+                        src = nw[k > 0 ? k - 1 : 0];
+                    if (m == 0) {
+                        float sr0, si0;
+                        cf_parts(src, sr0, si0);
+                        nw[k] = cf_make(fmaf(2.f * LX[k], br0, fmaf(2.f * LY[k], bi0, fmaf(-LZ[k], cr0, sr0))), 0.f);
+                    } else {
+                        nw[k] = cf_stencil_nb(nbk, c, src, X2[k], YmY[k], nZ2[k]);
+                    }
+                    R[k][m] = nw[k];
+                }
+                if (want0) {
+                    float vr, vi;
+                    cf_parts(nw[OUT], vr, vi);
+                    trow0[m * LD] = (m & 1) ? vi : vr;
+                    if (m > 0) trow0[-m * LD] = (m & 1) ? vr : vi;
                 }
             }
             if (n == pw || (n + 2) * (n + 2) - nb * nb > CAP) {
