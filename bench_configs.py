@@ -367,7 +367,7 @@ def run_galerkin(args, dev):
     wn = w.cpu().numpy()
     ref = np.sum(P * wn[leaf_of[el]], axis=1)
     err = float(np.max(np.abs(got[el] - ref) / np.sum(np.abs(P * wn[leaf_of[el]]), axis=1)))
-    flops = (element_flops("triangle", "const", ("single",), p) + (p + 1) ** 2) * n_elem
+    flops = (element_flops("triangle", "const", ("single",), p, point="order") + (p + 1) ** 2) * n_elem
     _emit({"metric": "Galerkin element integrals/s (local expansion over each receiving triangle)",
            "value": n_elem / (ms * 1e-3), "unit": "elements/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
@@ -380,7 +380,7 @@ def run_galerkin(args, dev):
 
 def run_biot_savart(args, dev):
     import paper_2107_10942_gb300 as q
-    from paper_2107_10942_gb300.roofline import level_flops
+    from paper_2107_10942_gb300.roofline import level_flops, point_level_order_flops
     from paper_2107_10942_gb300.upward import Upward
     p = 12
     m = W.cfg_mixed_ball()
@@ -412,7 +412,7 @@ def run_biot_savart(args, dev):
     plan.sync()
     per_step = 3 * n_elem * (p + 1) ** 2
     # one recursion (the segment chain's two levels) and three weighted sums (one FMA per column each)
-    flops = (2 * level_flops(p) + 3 * 2 * (p + 1) ** 2) * n_elem
+    flops = (point_level_order_flops(p) + level_flops(p) + 3 * 2 * (p + 1) ** 2) * n_elem
     _emit({"metric": "vector line-density Q2X element-moments/s (three components, Eq. st3)",
            "value": per_step / (ms_q2x * 1e-3), "unit": "element-moments/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_q2x, "higher_is_better": True, "dtype": "f64",

@@ -404,6 +404,35 @@ __device__ __forceinline__ int col_desc(int c)
     return (int)__ldg(&g_coltab.v[c]);
 }
 
+// Point level in the FP64 path: recursion over the order at a fixed degree.
+// Reading the point stencil of Eqs. (rec2), (rec10), (rec11) as multiplication
+// by the Laurent polynomial f(w) = -xi w - z + eta / w (xi = (x + iy)/2,
+// eta = conj xi, z of the level's vertex) gives T_n^m = seed [w^m] f(w)^n.
+// The coefficients of g = f^n satisfy f g' = n f' g; comparing the powers w^m
+// gives, with T_n^m = (-xi)^m Q_n^m and 4 |xi|^2 = x^2 + y^2,
+//   (n - m) Q_n^m = -(m + 1) z Q_n^{m+1} - (n + m + 2) |xi|^2 Q_n^{m+2},
+// Q_n^n = 1, Q_n^{n-1} = -n z: a real recursion downwards in m that needs no
+// row of the previous degree.  Q_n^m is a polynomial in z and |xi|^2, so the
+// recursion has no division by |xi| and stays accurate near the axis (checked
+// against exact rational arithmetic to p = 20).  Per entry it costs six FP64
+// operations against ten for the stencil.  A(n, m) = -(m + 1)/(n - m) and
+// B(n, m) = -(n + m + 2)/(n - m) for m <= n - 2.
+struct QTab {
+    double a[(Q2X_P_MAX + 1) * (Q2X_P_MAX + 1)];
+    double b[(Q2X_P_MAX + 1) * (Q2X_P_MAX + 1)];
+};
+constexpr QTab make_q_tab()
+{
+    QTab t{};
+    for (int n = 0; n <= Q2X_P_MAX; ++n)
+        for (int m = 0; m + 2 <= n; ++m) {
+            t.a[n * (Q2X_P_MAX + 1) + m] = -(double)(m + 1) / (double)(n - m);
+            t.b[n * (Q2X_P_MAX + 1) + m] = -(double)(n + m + 2) / (double)(n - m);
+        }
+    return t;
+}
+static __device__ const QTab g_qtab = make_q_tab();
+
 // final coefficient of column (n, m) (its descriptor from col_desc) from a
 // sum acc: acc * sign / (n+d)! (/ 4pi for COEFF) * 2^(s (n + shift_n0)), the
 // power of two being the leaf scale of the frame (exact).
@@ -1190,61 +1219,112 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
             }
         }
     } else {
-        // ---- FP64: scalar arithmetic, exact order bounds; the last two
-        // orders of each degree use specialised bodies without the
-        // neighbours that are known to vanish (b = 0 at m = n-1, b = c = 0
-        // at m = n), so no DFMA is spent on zero operands.
+        // ---- FP64: scalar arithmetic, exact order bounds, orders from n down
+        // to 0.  Level 0 (the point level) is T_n^m = w_m Q_n^m with the
+        // element's w_m = seed (-xi)^m (its row: computed once, read-only)
+        // and Q_n^m from the order recursion of g_qtab, carried in two
+        // scalars.  Levels k >= 1 use the stencil: the old entry m - 1 is
+        // still in the row, the old entry m + 1 is carried down from the
+        // previous order.  The first two orders of each degree (m = n, n - 1)
+        // use specialised bodies without the neighbours known to vanish, so no
+        // DFMA is spent on zero operands.
         T Rr[NL][P + 1], Ri[NL][P + 1];
 #pragma unroll
         for (int k = 0; k < NL; ++k)
 #pragma unroll
             for (int m = 0; m <= P; ++m) Rr[k][m] = Ri[k][m] = T(0);
+        {
+            T wr = seed, wi = T(0);
+            const T mx = -LX[0], my = -LY[0];
+            static_for<0, P + 1>([&](auto m_c) {
+                constexpr int m = decltype(m_c)::value;
+                if (m <= pw) {
+                    if (m > 0) {
+                        const T tr = fma(wr, mx, -wi * my);
+                        wi = fma(wr, my, wi * mx);
+                        wr = tr;
+                    }
+                    if (NS > 0)
+                        srows[m * 32 + lane] = make_double2(wr, wi);
+                    else
+                        Rr[0][m] = wr, Ri[0][m] = wi;
+                }
+            });
+        }
+        const T zq = LZ[0], x2q = fma(LX[0], LX[0], LY[0] * LY[0]);  // z and |xi|^2 of the point level
 #pragma unroll 1
         for (int n = 0; n <= pw; ++n) {
             T* trow0 = tile + (n * n - nb * nb + n) * LD + lane;
             T* trow1 = trow0 + CH * LD;
             const T c2 = T(n + 1) * s2;
-            const T sd = (n == 0) ? seed : T(0);
-            T pr[NL], pi[NL];
+            const T nz = -T(n) * zq;  // Q_n^{n-1}
+            const double* qa = g_qtab.a + n * (Q2X_P_MAX + 1);
+            const double* qb = g_qtab.b + n * (Q2X_P_MAX + 1);
+            T Q1 = T(0), Q2 = T(0);   // Q_n^{m+1}, Q_n^{m+2}
+            T br[NL], bi[NL];         // old entry m + 1 of each level
 #pragma unroll
-            for (int k = 0; k < NL; ++k) pr[k] = pi[k] = T(0);
-            // body of order m; HB: neighbour m+1 present, HC: entry m present
+            for (int k = 0; k < NL; ++k) br[k] = bi[k] = T(0);
+            // body of order m; HB: old entry m + 1 present, HC: old entry m present
             auto body = [&](auto m_c, auto hb_c, auto hc_c) {
                 constexpr int m = decltype(m_c)::value;
                 constexpr bool HB = decltype(hb_c)::value && (m < P);
                 constexpr bool HC = decltype(hc_c)::value;
                 T nr[NL], ni[NL];
+                {
+                    T Q;
+                    if (!HC)
+                        Q = T(1);  // m = n
+                    else if (!HB)
+                        Q = nz;  // m = n - 1
+                    else
+                        Q = fma(__ldg(qa + m) * zq, Q1, (__ldg(qb + m) * x2q) * Q2);
+                    Q2 = Q1;
+                    Q1 = Q;
+                    T wr, wi;
+                    if (NS > 0) {
+                        const double2 v = srows[m * 32 + lane];
+                        wr = v.x, wi = v.y;
+                    } else {
+                        wr = Rr[0][m], wi = Ri[0][m];
+                    }
+                    if (HC) {
+                        nr[0] = wr * Q;
+                        ni[0] = (m == 0) ? T(0) : wi * Q;
+                    } else {
+                        nr[0] = wr;
+                        ni[0] = (m == 0) ? T(0) : wi;
+                    }
+                }
 #pragma unroll
-                for (int k = 0; k < NL; ++k) {
-                    T cr = T(0), ci = T(0), br = T(0), bi = T(0);
+                for (int k = 1; k < NL; ++k) {
+                    // degree n-1 entries m - 1 (a) and m (c) from the row; m + 1 (b) carried
+                    T ar = T(0), ai = T(0), cr = T(0), ci = T(0);
+                    const T bR = HB ? br[k] : T(0), bI = HB ? bi[k] : T(0);
                     if (k < NS) {
-                        // degree n-1 entries m and m+1 of a shared-memory row
-                        // (entries above n-1 are never read, so the rows need
-                        // no clearing between elements)
+                        if (m > 0) {
+                            const double2 v = srows[(k * (P + 1) + (m > 0 ? m - 1 : 0)) * 32 + lane];
+                            ar = v.x, ai = v.y;
+                        }
                         if (HC) {
                             const double2 v = srows[(k * (P + 1) + m) * 32 + lane];
                             cr = v.x, ci = v.y;
                         }
-                        if (HB) {
-                            const double2 v = srows[(k * (P + 1) + (m < P ? m + 1 : P)) * 32 + lane];
-                            br = v.x, bi = v.y;
-                        }
                     } else {
+                        if (m > 0) ar = Rr[k][m > 0 ? m - 1 : 0], ai = Ri[k][m > 0 ? m - 1 : 0];
                         if (HC) cr = Rr[k][m], ci = Ri[k][m];
-                        if (HB) br = Rr[k][m < P ? m + 1 : P], bi = Ri[k][m < P ? m + 1 : P];
                     }
                     if (KIND == KIND_TRI && k == OUT && want1) {
                         T dr = T(0), di = T(0);
                         if (m == 0) {
-                            if (HB) dr = fma(T(2) * XN, br, fma(T(2) * YN, bi, dr));
+                            if (HB) dr = fma(T(2) * XN, bR, fma(T(2) * YN, bI, dr));
                             if (HC) dr = fma(-ZN, cr, dr);
                         } else {
                             if (HB) {
-                                dr = fma(XN, br - pr[k], fma(YN, bi + pi[k], dr));
-                                di = fma(XN, bi - pi[k], fma(-YN, br + pr[k], di));
+                                dr = fma(XN, bR - ar, fma(YN, bI + ai, dr));
+                                di = fma(XN, bI - ai, fma(-YN, bR + ar, di));
                             } else {
-                                dr = fma(-XN, pr[k], fma(YN, pi[k], dr));
-                                di = fma(-XN, pi[k], fma(-YN, pr[k], di));
+                                dr = fma(-XN, ar, fma(YN, ai, dr));
+                                di = fma(-XN, ai, fma(-YN, ar, di));
                             }
                             if (HC) {
                                 dr = fma(-ZN, cr, dr);
@@ -1255,10 +1335,7 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                         if (m > 0) trow1[-m * LD] = (m & 1) ? dr : di;
                     }
                     T sr, si;
-                    if (k == 0) {
-                        sr = (m == 0) ? sd : T(0);
-                        si = T(0);
-                    } else if (LIN && k == 2) {
+                    if (LIN && k == 2) {
                         sr = fma(c2, nr[0], s3 * nr[1]);
                         si = fma(c2, ni[0], s3 * ni[1]);
                     } else if (LIN && k == 3) {
@@ -1268,20 +1345,20 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                         sr = fma(s1, nr[3], nr[2]);
                         si = fma(s1, ni[3], ni[2]);
                     } else {
-                        sr = nr[k > 0 ? k - 1 : 0];
-                        si = ni[k > 0 ? k - 1 : 0];
+                        sr = nr[k - 1];
+                        si = ni[k - 1];
                     }
                     T vr = sr, vi = (m == 0) ? T(0) : si;
                     if (m == 0) {
-                        if (HB) vr = fma(T(2) * LY[k], bi, fma(T(2) * LX[k], br, vr));
+                        if (HB) vr = fma(T(2) * LY[k], bI, fma(T(2) * LX[k], bR, vr));
                         if (HC) vr = fma(-LZ[k], cr, vr);
                     } else {
                         if (HB) {
-                            vr = fma(LY[k], bi + pi[k], fma(LX[k], br - pr[k], vr));
-                            vi = fma(-LY[k], br + pr[k], fma(LX[k], bi - pi[k], vi));
+                            vr = fma(LY[k], bI + ai, fma(LX[k], bR - ar, vr));
+                            vi = fma(-LY[k], bR + ar, fma(LX[k], bI - ai, vi));
                         } else {
-                            vr = fma(LY[k], pi[k], fma(-LX[k], pr[k], vr));
-                            vi = fma(-LY[k], pr[k], fma(-LX[k], pi[k], vi));
+                            vr = fma(LY[k], ai, fma(-LX[k], ar, vr));
+                            vi = fma(-LY[k], ar, fma(-LX[k], ai, vi));
                         }
                         if (HC) {
                             vr = fma(-LZ[k], cr, vr);
@@ -1290,8 +1367,8 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                     }
                     nr[k] = vr;
                     ni[k] = vi;
-                    pr[k] = cr;
-                    pi[k] = ci;
+                    br[k] = cr;
+                    bi[k] = ci;
                     if (k < NS) {
                         srows[(k * (P + 1) + m) * 32 + lane] = make_double2(vr, vi);
                     } else {
@@ -1307,14 +1384,15 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
             };
             using TT = std::integral_constant<bool, true>;
             using FF = std::integral_constant<bool, false>;
-            static_for<0, P + 1>([&](auto m_c) {
-                constexpr int m = decltype(m_c)::value;
+            static_for<0, P + 1>([&](auto i_c) {
+                constexpr int m = P - decltype(i_c)::value;
+                using MC = std::integral_constant<int, m>;
                 if (m + 1 < n)
-                    body(m_c, TT{}, TT{});
+                    body(MC{}, TT{}, TT{});
                 else if (m + 1 == n)
-                    body(m_c, FF{}, TT{});
+                    body(MC{}, FF{}, TT{});
                 else if (m == n)
-                    body(m_c, FF{}, FF{});
+                    body(MC{}, FF{}, FF{});
             });
             if (n == pw || (n + 2) * (n + 2) - nb * nb > CAP) {
                 __syncwarp();

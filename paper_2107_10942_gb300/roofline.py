@@ -11,7 +11,11 @@ with a = x^{m-1}, b = x^{m+1}, c = x^m of degree n-1.  Only terms whose operand
 exists (|order| <= n-1) are counted: 4 adds + 4 FMAs for the xi/eta pair when
 both a and b exist, 4 FMAs when only a does, 2 FMAs for the z term, 2 FMAs
 for m = 0's eta term; the source rides in the FMA addend.  FMA = 2 flops.
-The leaf reduction adds one flop per element and output column."""
+The leaf reduction adds one flop per element and output column.
+
+The FP64 kernels compute the point level (level 0) by a recursion over the
+order at fixed degree instead of the stencil (`point="order"`, counted by
+`point_level_order_flops`); the FP32 kernels use the stencil for every level."""
 from __future__ import annotations
 
 # GB300 (recipe figures): 152 SMs, 2070 MHz maximum SM clock; FP32: 128 lanes
@@ -36,20 +40,38 @@ def level_flops(p: int) -> int:
     return sum(stencil_flops(n, m) for n in range(p + 1) for m in range(n + 1))
 
 
-def element_flops(kind: str, density: str = "const", layers=("single",), p: int = 12) -> int:
-    """Flops per element of one Q2X pass (recursion + double layer + reduction)."""
+def point_level_order_flops(p: int) -> int:
+    """Flops per element of the FP64 kernels' point level: the element's row
+    w_m = seed (-xi)^m (a complex multiply, 6 flops, per m >= 1) and |xi|^2
+    (3 flops); per degree n >= 1, Q_n^{n-1} = -n z (1 flop); per entry, none at
+    m = n (T_n^n = w_n), the order recursion at m <= n - 2 (three multiplies
+    and one FMA, 5 flops) and the product w_m Q_n^m at m <= n - 1 (2 flops,
+    1 at m = 0 where w_0 is real)."""
+    f = 6 * p + 3
+    for n in range(1, p + 1):
+        f += 1
+        for m in range(n):
+            f += (1 if m == 0 else 2) + (5 if m <= n - 2 else 0)
+    return f
+
+
+def element_flops(kind: str, density: str = "const", layers=("single",), p: int = 12,
+                  point: str = "stencil") -> int:
+    """Flops per element of one Q2X pass (recursion + double layer + reduction).
+    point: "stencil" (FP32 kernels) or "order" (FP64 kernels) for level 0."""
     L = level_flops(p)
+    L0 = L if point == "stencil" else point_level_order_flops(p)
     entries = sum(n + 1 for n in range(p + 1))
     if kind == "segment":
-        f = 2 * L
+        f = L0 + L
     elif kind == "tetra":
-        f = 4 * L
+        f = L0 + 3 * L
     elif density == "const":
-        f = 3 * L
+        f = L0 + 2 * L
     else:
         # 5 levels; E source c2 q + s3 j (1 mul + 1 fma per part) and Iw source
         # s1 i + E (1 fma per part); m = 0 entries are real
-        f = 5 * L + 6 * entries - 3 * (p + 1) + 4 * entries - 2 * (p + 1) + (p + 1)
+        f = L0 + 4 * L + 6 * entries - 3 * (p + 1) + 4 * entries - 2 * (p + 1) + (p + 1)
     if "double" in layers:
         f += L
     f += len(layers) * (p + 1) ** 2
