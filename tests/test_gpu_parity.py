@@ -87,6 +87,37 @@ def test_parity(q2x, orc, kind, density, layer, both, prec, p):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind,density,layer,both", CASES)
+def test_point_vertex_on_axis_and_plane(q2x, orc, kind, density, layer, both, prec):
+    """The point level's vertex (the element's second) on its leaf centre's
+    z-axis, in the centre's z-plane or at the centre itself: x + iy = 0 or
+    z = 0 exactly, the cases where the FP64 order recursion over m (reading
+    R27) would be ill-conditioned if it divided by |xi|.  p = 20."""
+    p = 20
+    prob = random_problem(kind, SIZES, seed=2701 + len(kind), p=p, density=density)
+    n = prob["idx"].shape[1]
+    leaf_of = np.repeat(np.arange(prob["leaf_c"].shape[1]), np.diff(prob["leaf_off"]))
+    v2 = prob["idx"][1]
+    c = prob["leaf_c"][:, leaf_of]
+    sel = np.arange(n) % 4
+    prob["vxyz"][0, v2[sel == 0]] = c[0, sel == 0]  # on the axis
+    prob["vxyz"][1, v2[sel == 0]] = c[1, sel == 0]
+    prob["vxyz"][2, v2[sel == 1]] = c[2, sel == 1]  # in the plane
+    prob["vxyz"][:, v2[sel == 2]] = c[:, sel == 2]  # at the centre
+    rho = W.leaf_rho(prob["vxyz"], prob["idx"], prob["leaf_off"], prob["leaf_c"])
+    prob["leaf_rho"] = np.where(rho > 0, rho, 1.0)
+    single = layer == 0 or both
+    double = layer == 1 or both
+    cs, cd = run(q2x, prob, prec, single=single, double=double)
+    for ly, on, got in ((0, single, cs), (1, double, cd)):
+        if not on:
+            continue
+        ref = oracle_coef(orc, prob, layer=ly)
+        e = norm_err(got, ref, p, prob["leaf_rho"], ly)
+        assert e <= TOL[prec], (ly, e)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("kind,density,layer,both", [("segment", "const", 0, False),
                                                      ("triangle", "const", 0, True),
                                                      ("tetra", "const", 0, False)])
