@@ -431,7 +431,7 @@ constexpr QTab make_q_tab()
         }
     return t;
 }
-static __device__ const QTab g_qtab = make_q_tab();
+static __constant__ QTab g_qtab = make_q_tab();  // warp-uniform reads: the constant cache
 
 // final coefficient of column (n, m) (its descriptor from col_desc) from a
 // sum acc: acc * sign / (n+d)! (/ 4pi for COEFF) * 2^(s (n + shift_n0)), the
@@ -1277,7 +1277,7 @@ __device__ __forceinline__ void run_chain(const Frame<T, Chain<KIND, DENS>::NL>&
                     else if (!HB)
                         Q = nz;  // m = n - 1
                     else
-                        Q = fma(__ldg(qa + m) * zq, Q1, (__ldg(qb + m) * x2q) * Q2);
+                        Q = fma(qa[m] * zq, Q1, (qb[m] * x2q) * Q2);
                     Q2 = Q1;
                     Q1 = Q;
                     T wr, wi;
