@@ -24,6 +24,10 @@
 // The 1/(n+d)! goes into the per-column output constant.  All levels start
 // from q^_0 = seed and zero rows at n = -1, which reproduces the starting
 // values of Eq. (rec3) (p_0 = j_0 = 1, i_0 = b_0 = 1/2, a_0 = 1/6).
+// The FP64 kernels compute the point level q^ by an equivalent recursion
+// over the order at fixed degree (see g_qtab below) and run the degree's
+// orders from n down to 0; the FP32 kernels run the stencil on every level,
+// orders 0 up to n.
 //
 // Linear density on triangles (not in the paper; derived by the same
 // integration by parts as Lemma 2 with the weight w = s1(1-u-v) + s2 u + s3 v):
