@@ -66,9 +66,9 @@ DEFAULT_WORKLOAD = "sphere-L9-const"
 # 4 x FFMA2 + 2 x FFMA + 2 x FADD2 + 2 x FMUL2 + FADD + FMUL (per-opcode thread counts:
 # the packed instructions are not in the FFMA/FADD class counters).
 KERNEL_COUNTERS = {
-    ("sphere-L9-const", "fp64"): dict(traffic=218668288 + 111515904, executed_flops=29402290440),
+    ("sphere-L9-const", "fp64"): dict(traffic=218932480 + 111733248, executed_flops=29402290440),
     ("sphere-L9-const", "fp32"): dict(traffic=177844224 + 104552192, executed_flops=47011848132),
-    ("sphere-L7-linear", "fp64"): dict(traffic=9514752 + 29184, executed_flops=2644445248),
+    ("sphere-L7-linear", "fp64"): dict(traffic=9516288 + 23808, executed_flops=2644445248),
     ("sphere-L7-linear", "fp32"): dict(traffic=9379072 + 512, executed_flops=3266600364),
 }
 COUNTER_SOURCE = "ncu --set full capture of one launch of this kernel on this workload"
