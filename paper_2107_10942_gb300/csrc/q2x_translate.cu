@@ -32,6 +32,7 @@ constexpr int TR_WARPS = 4;
 struct TransArgs {
     int p, np, n_out, norm, accumulate;
     int cta_per_source;  // 1: the four warps of a CTA share one source's terms
+    int cta_per_dst;     // 1: the combine gives each destination a CTA of four warps
     int64_t n_src, n_dst;
     const double* src_coef;
     const double* src_c;
@@ -51,7 +52,8 @@ __device__ void build_r(double2* Rc, int p, double tx, double ty, double tz, int
 
 // Packed real row of R(t) (Re at n^2+n+m, Im at n^2+n-m, m > 0) unpacked
 // into Rc and -Rc (R_n^{-m} = (-1)^m conj R_n^m); one warp.
-__device__ void unpack_r(double2* Rc, const double* __restrict__ row, int np, int lane);
+// (threads tid, tid + nthr, ... of the warp or CTA that shares Rc)
+__device__ void unpack_r(double2* Rc, const double* __restrict__ row, int np, int tid, int nthr);
 
 // degree and order of output o = n(n+1)/2 + m, 0 <= m <= n
 __device__ __forceinline__ void out_nm(int o, int& n, int& m)
@@ -168,9 +170,9 @@ __device__ void build_r(double2* Rc, int p, double tx, double ty, double tz, int
     }
 }
 
-__device__ void unpack_r(double2* Rc, const double* __restrict__ row, int np, int lane)
+__device__ void unpack_r(double2* Rc, const double* __restrict__ row, int np, int tid, int nthr)
 {
-    for (int k = lane; k < np; k += 32) {
+    for (int k = tid; k < np; k += nthr) {
         int n, m;
         col_nm(k, n, m);
         const int am = m < 0 ? -m : m;
@@ -243,10 +245,15 @@ __global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransA
     }
     const int64_t d = lo;
 
-    if (!cta || wib == 0) {
+    // with precomputed R(t) rows every warp of a CTA takes part in filling
+    // the shared copy; the recursion for R(t) is one warp's
+    const bool rt_mode = a.rt != nullptr;
+    const int tid = (cta && rt_mode) ? (int)threadIdx.x : lane;
+    const int nthr = (cta && rt_mode) ? TR_WARPS * 32 : 32;
+    if (!cta || rt_mode || wib == 0) {
         // ---- complex source row F[n][m], m = -n..n (Eq. (bas2.1) for m < 0)
         const double* src = a.src_coef + s * (int64_t)np;
-        for (int k = lane; k < np; k += 32) {
+        for (int k = tid; k < np; k += nthr) {
             int n, m;
             col_nm(k, n, m);
             const int am = m < 0 ? -m : m;
@@ -262,13 +269,13 @@ __global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransA
         if (a.rt) {
             int ti = __ldg(a.t_idx + s);
             if (ti < 0 || ti >= a.n_t) {
-                if (lane == 0) atomicOr(a.err, 1u);
+                if (tid == 0) atomicOr(a.err, 1u);
                 ti = -1;
             }
             if (ti >= 0) {
-                unpack_r(Rc, a.rt + (int64_t)ti * np, np, lane);
+                unpack_r(Rc, a.rt + (int64_t)ti * np, np, tid, nthr);
             } else {
-                for (int k = lane; k < np; k += 32) Rc[k] = Rc[TR_NP_MAX + k] = make_double2(0.0, 0.0);
+                for (int k = tid; k < np; k += nthr) Rc[k] = Rc[TR_NP_MAX + k] = make_double2(0.0, 0.0);
             }
             __syncwarp();
         } else {
@@ -363,11 +370,15 @@ __global__ void __launch_bounds__(TR_WARPS * 32) q2x_translate_rows(const TransA
     }
 }
 
-// One warp per destination: its sources' rows added in source order, packed.
+// One warp per destination (few destinations, the top of a tree: a CTA of
+// four warps per destination, its outputs split over 128 threads): its
+// sources' rows added in source order, packed.
 __global__ void q2x_translate_combine(const TransArgs a)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t d = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = a.cta_per_dst ? (int)threadIdx.x : (int)(threadIdx.x & 31);
+    const int nthr = a.cta_per_dst ? (int)blockDim.x : 32;
+    const int64_t d = a.cta_per_dst ? (int64_t)blockIdx.x
+                                    : (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (d >= a.n_dst) return;
     int64_t s0 = __ldg(a.dst_off + d), s1 = __ldg(a.dst_off + d + 1);
     if (s0 < 0 || s1 < s0 || s1 > a.n_src || (d == 0 && s0 != 0) || (d == a.n_dst - 1 && s1 != a.n_src)) {
@@ -375,7 +386,7 @@ __global__ void q2x_translate_combine(const TransArgs a)
         s0 = s1 = 0;
     }
     double* out = a.dst_coef + d * (int64_t)a.np;
-    for (int o = lane; o < a.n_out; o += 32) {
+    for (int o = lane; o < a.n_out; o += nthr) {
         double2 v = make_double2(0.0, 0.0);
 #pragma unroll 4
         for (int64_t s = s0; s < s1; ++s) {
@@ -416,6 +427,7 @@ static q2x_status translate_impl(q2x_plan_t plan, int p, int64_t n_src, const do
     if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "cudaSetDevice");
     q2x::TransArgs a;
     a.cta_per_source = 0;
+    a.cta_per_dst = (n_dst <= (int64_t)plan->num_sms) ? 1 : 0;
     a.p = p;
     a.np = (p + 1) * (p + 1);
     a.n_out = (p + 1) * (p + 2) / 2;
@@ -449,7 +461,7 @@ static q2x_status translate_impl(q2x_plan_t plan, int p, int64_t n_src, const do
         if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "q2x_translate_rows launch");
         plan->launches += 1;
     }
-    q2x::q2x_translate_combine<<<(unsigned)((n_dst + 3) / 4), 128, 0, plan->stream>>>(a);
+    q2x::q2x_translate_combine<<<(unsigned)(a.cta_per_dst ? n_dst : (n_dst + 3) / 4), 128, 0, plan->stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return q2x_cuda_fail(plan, e, "q2x_translate_combine launch");
     plan->launches += 1;
