@@ -152,26 +152,42 @@ __global__ void leaf_tile_fill_kernel(const int64_t* leaf_off, int64_t n_leaves,
     }
 }
 
-// one warp per leaf
+// one warp per 32 leaves: each lane reads one leaf's slot and element
+// ranges; the warp then handles, one after the other, the leaves that have
+// work (several tiles: their partial rows summed in slot order; empty and
+// not accumulating: a zero row), columns over the lanes
 __global__ void leaf_tile_combine_kernel(const double* __restrict__ partial, const int64_t* __restrict__ slot_off,
                                          const int64_t* __restrict__ leaf_off, int np, int64_t n_leaves, double* coef,
                                          int accumulate)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t L = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (L >= n_leaves) return;
-    const int64_t s0 = slot_off[L], s1 = slot_off[L + 1];
-    if (s1 == s0) {
-        // a single-tile leaf wrote its own row; an empty leaf is zero
-        if (!accumulate && __ldg(leaf_off + L + 1) == __ldg(leaf_off + L))
-            for (int c = lane; c < np; c += 32) coef[L * np + c] = 0.0;
-        return;
+    const int64_t L0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+    if (L0 >= n_leaves) return;  // warp-uniform
+    const int64_t L = L0 + lane;
+    long long s0 = 0, s1 = 0;
+    bool work = false;
+    if (L < n_leaves) {
+        s0 = slot_off[L];
+        s1 = slot_off[L + 1];
+        const bool empty = __ldg(leaf_off + L + 1) == __ldg(leaf_off + L);
+        // a single-tile leaf wrote its own row
+        work = s1 > s0 || (empty && !accumulate);
     }
-    for (int c = lane; c < np; c += 32) {
-        double acc = 0.0;
-        for (int64_t s = s0; s < s1; ++s) acc += partial[s * np + c];
-        double* d = coef + L * np + c;
-        *d = accumulate ? *d + acc : acc;
+    unsigned mask = __ballot_sync(0xffffffffu, work);
+    while (mask) {
+        const int r = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const long long a0 = __shfl_sync(0xffffffffu, s0, r), a1 = __shfl_sync(0xffffffffu, s1, r);
+        double* row = coef + (L0 + r) * np;
+        if (a1 == a0) {  // an empty leaf is zero
+            for (int c = lane; c < np; c += 32) row[c] = 0.0;
+        } else {
+            for (int c = lane; c < np; c += 32) {
+                double acc = 0.0;
+                for (long long sl = a0; sl < a1; ++sl) acc += partial[sl * np + c];
+                row[c] = accumulate ? row[c] + acc : acc;
+            }
+        }
     }
 }
 
@@ -191,7 +207,8 @@ cudaError_t leaf_tiles_combine(const double* partial, const int64_t* slot_off, c
                                int64_t n_leaves, double* coef, int accumulate, cudaStream_t st)
 {
     const int warps = 8;
-    leaf_tile_combine_kernel<<<(unsigned)((n_leaves + warps - 1) / warps), warps * 32, 0, st>>>(
+    const int64_t n_warps = (n_leaves + 31) / 32;
+    leaf_tile_combine_kernel<<<(unsigned)((n_warps + warps - 1) / warps), warps * 32, 0, st>>>(
         partial, slot_off, leaf_off, np, n_leaves, coef, accumulate);
     return cudaGetLastError();
 }
